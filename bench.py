@@ -1,0 +1,359 @@
+"""Benchmark: FIT leapfrog + ParaExp on GB300, Gcell-updates/s and % of HBM roofline.
+
+One step = one complete ParaExp solve of the workload through the C ABI:
+create the grid from device-resident per-cell materials (material checks and
+the FP64 coefficient build), advance all K window members batched (leapfrog
+for the inhomogeneous and the homogeneous problems), superpose probe traces
+and final fields in FP64, destroy the grid.  Default workload: 256^3 cells,
+40 lossy dielectric boxes, 20000 steps, K = 16 windows (2.85e12 cell-updates).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload boxes256|cavity16]
+
+Under torchrun each rank solves its own copy of the workload (independent
+problems, no collective on the data path: weak scaling); rank 0 prints one
+JSON line.  ``--impl reference`` times the serial FP64 CPU oracle instead, on
+a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FIT leapfrog Gcell-updates/s (% HBM roofline); batched ParaExp & adjoint vs plain"
+UNIT = "Gcell-updates/s"
+L2_BYTES = 129e6
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="boxes256")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--compare-plain", action="store_true",
+                    help="also time the K windows run one after another (members_per_pass=1)")
+    return ap.parse_args()
+
+
+def load_workload(name):
+    from paper_1705_08019_gb300 import workloads as W
+    if name == "boxes256":
+        return W.boxes256()
+    if name == "cavity16":
+        return W.cavity16()
+    if name == "boxes512":
+        return W.boxes512()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def config_of(w, extra=None):
+    nx, ny, nz = w.dims
+    state_bytes = 2 * 6 * (4 if w.precision == 32 else 8) * w.ncell * w.K
+    cfg = {"workload": w.name, "cells": f"{nx}x{ny}x{nz}", "nsteps": w.nsteps, "K": w.K,
+           "precision": f"fp{w.precision}", "lossy": w.sigma is not None,
+           "l2": ("inputs larger than L2: %.1f GB of member state" % (state_bytes / 1e9))
+           if state_bytes > L2_BYTES else "fits in L2 (small case)",
+           "parallelism": "replicas (independent problems per GPU)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def work_of(w):
+    """cell-updates of one ParaExp solve with equal windows (Sec. III)."""
+    win = w.windows()
+    return int(sum(int(win[-1] - win[j]) for j in range(w.K))) * w.ncell
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(w, nsteps=4, K=2):
+    """Time the FP64 serial oracle on a bounded sample of the workload: the
+    full grid (coefficients included) and a ParaExp solve of `nsteps` steps in
+    K windows.  Returns (cell-updates/s, seconds, description)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    dt = w.cfl_fraction * oracle.cfl_dt(w.dims, w.spacing, w.eps_r, w.mu_r)
+    g = oracle.OracleGrid(w.dims, w.spacing, w.eps_r, w.mu_r, w.sigma, dt=dt, round32=(w.precision == 32))
+    win = np.array([(j * nsteps) // K for j in range(K + 1)], dtype=np.int64)
+    g.paraexp(K, win, w.sources, w.probes)
+    sec = time.perf_counter() - t0
+    work = int(sum(int(win[-1] - win[j]) for j in range(K))) * w.ncell
+    desc = (f"oracle (serial FP64 C) on the full {w.dims[0]}x{w.dims[1]}x{w.dims[2]} grid: coefficient build + "
+            f"ParaExp of {nsteps} steps in {K} windows ({work:.3g} cell-updates)")
+    return work / sec / 1e9, sec, desc
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = load_workload(args.workload)
+    for _ in range(args.warmup):
+        oracle_sample(w)
+    secs, rate, desc = [], None, None
+    for _ in range(args.steps):
+        rate, sec, desc = oracle_sample(w)
+        secs.append(sec)
+    ms = 1000.0 * sum(secs) / len(secs)
+    value = float(rate)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(w, {"sample": desc}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    """Sample SM clocks and throttle reasons with nvidia-smi during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.remove(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def traffic_from_profile():
+    """Measured DRAM bytes / algorithmic bytes of the step kernel from the
+    committed ncu summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_boxes256.txt")
+    src = os.path.join(ROOT, "paper_1705_08019_gb300", "csrc", "step.cu")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and not line.startswith(" "):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if vals.get("step_cu_sha256") != sha:
+        return None
+    try:
+        return float(vals["dram_over_algorithmic"])
+    except (KeyError, ValueError):
+        return None
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1705_08019_gb300 import build as B
+    from paper_1705_08019_gb300 import fitgb
+    B.build()
+    fitgb.load()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    w = load_workload(args.workload)
+    T = torch.float32 if w.precision == 32 else torch.float64
+    nx, ny, nz = w.dims
+    eps_d = torch.from_numpy(w.eps_r).to(dev)
+    sig_d = torch.from_numpy(w.sigma).to(dev) if w.sigma is not None else None
+    mu_d = torch.from_numpy(w.mu_r).to(dev) if w.mu_r is not None else None
+    win = w.windows()
+    nt = int(win[-1] - win[0])
+    probe_d = torch.zeros((nt, len(w.probes)), dtype=torch.float64, device=dev)
+    ef_d = torch.zeros((3, nz, ny, nx), dtype=torch.float64, device=dev)
+    hf_d = torch.zeros((3, nz, ny, nx), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    g0 = fitgb.fit_grid_create(w.dims, w.spacing, eps_d, mu_d, sig_d, w.precision)
+    dt = w.cfl_fraction * fitgb.fit_cfl_dt(g0)
+    fitgb.fit_grid_destroy(g0)
+
+    def step(profile=True, members_per_pass=0):
+        g = fitgb.fit_grid_create(w.dims, w.spacing, eps_d, mu_d, sig_d, w.precision)
+        fitgb.paraexp_run(g, dt, w.K, win, w.sources, w.probes, probe_d, ef_d, hf_d,
+                          opts=fitgb.make_opts(profile=int(profile), members_per_pass=members_per_pass),
+                          stream=stream)
+        st = fitgb.fit_last_stats(g)
+        fitgb.fit_grid_destroy(g)
+        return st
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local_rank)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        stats.append(step())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    cells_per_step = stats[0]["cell_updates"]
+    assert cells_per_step == work_of(w), (cells_per_step, work_of(w))
+    value = world * cells_per_step / (ms / 1e3) / 1e9
+    step_ms = sum(s["step_ms"] for s in stats)
+    alg = sum(s["alg_bytes"] for s in stats)
+    launches = sum(s["step_launches"] for s in stats)
+    peak, peak_kind = peaks()
+    achieved = alg / (step_ms / 1e3) / 1e9 if step_ms > 0 else None
+    ratio = traffic_from_profile()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": (ratio * alg / launches) if ratio else None,
+            "peak_kind": f"{peak_kind} copy bandwidth",
+            "kernel": "step_kernel (fused E/H leapfrog, all active members)",
+            "alg_bytes_per_launch": alg / launches, "avg_launch_us": 1e3 * step_ms / launches,
+            "step_kernel_share": step_ms / (ms * args.steps)}
+    extras = {}
+    if args.compare_plain and rank == 0:
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(profile=False, members_per_pass=1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms = e0.elapsed_time(e1)
+        extras["plain_per_window_ms"] = plain_ms
+        extras["batched_speedup_vs_plain"] = plain_ms / ms
+
+    e2e = None
+    if not args.no_e2e:
+        # the same solve through the C ABI with host buffers: materials H2D,
+        # probe traces and superposed fields D2H, inside the timed region
+        pr_h = np.zeros((nt, len(w.probes)))
+        ef_h = np.zeros((3, nz, ny, nx))
+        hf_h = np.zeros((3, nz, ny, nx))
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        g = fitgb.fit_grid_create(w.dims, w.spacing, w.eps_r, w.mu_r, w.sigma, w.precision)
+        fitgb.paraexp_run(g, dt, w.K, win, w.sources, w.probes, pr_h, ef_h, hf_h)
+        e2e_s = time.perf_counter() - t0
+        fitgb.fit_grid_destroy(g)
+        if dist is not None:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        h2d = sum(a.nbytes for a in (w.eps_r, w.mu_r, w.sigma) if a is not None)
+        d2h = pr_h.nbytes + ef_h.nbytes + hf_h.nbytes
+        e2e = {"value": world * cells_per_step / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "seconds": e2e_s}
+        # the host results equal the device-resident ones
+        assert np.array_equal(pr_h, probe_d.cpu().numpy())
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, sec, desc = oracle_sample(w)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc, "seconds": sec,
+               "host_cores_available": os.cpu_count()}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32" if w.precision == 32 else "f64", "data": "synthetic",
+                "config": config_of(w), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(sum(s["kernel_launches"] for s in stats)), "clocks": ck}
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,232 @@
+/*
+ * fitgb.h -- C ABI of the GB300 FIT leapfrog + ParaExp library (libfitgb.so).
+ *
+ * Method: Merkel, Niyonzima, Schoeps, "ParaExp using Leapfrog as Integrator
+ * for High-Frequency Electromagnetic Simulations".
+ *   - Sec. II   FIT grid pair, curls C and C~ = C^T, material matrices
+ *               (eq. maxwell_grid1-3), the CFL estimate (eq. cfl), and the
+ *               interleaved discrete energy (eq. energy).
+ *   - Sec. II-A leapfrog update.
+ *   - Sec. III  ParaExp: zero-initial-value window problems, homogeneous
+ *               problems, superposition (Algorithm 1, eqs. solution-
+ *               particular-paraexp, solution-homogeneous-paraexp,
+ *               solution-particular-para, averaging1/2); here the homogeneous
+ *               problems are integrated by leapfrog as well.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid: nx*ny*nz cells of size dx*dy*dz [m]; PEC walls on all six sides.
+ * Per-cell arrays (eps_r, mu_r, sigma, gradients): nx*ny*nz values,
+ *   x fastest: c(i,j,k) = i + nx*(j + ny*k).
+ * Field arrays ("compact FIT layout"): component-major, then x fastest;
+ *   e = [e_x | e_y | e_z], h = [h_x | h_y | h_z], each component nx*ny*nz
+ *   values indexed like the cells.
+ *   e_a(i,j,k) is the voltage [V] on the primal edge from point (i,j,k) to
+ *   (i,j,k)+u_a.  h_a(i,j,k) is the magnetic voltage [A] on the dual edge
+ *   through the primal face normal to a whose lowest corner is (i,j,k).
+ *   The canonical FIT arrays of the paper have (nx+1)(ny+1)(nz+1) entries
+ *   per component; the entries with index nx, ny or nz along any axis are
+ *   identically zero under PEC (edges/faces in a wall or outside the box)
+ *   and are not stored.  Entries that are not degrees of freedom (e
+ *   tangential to a wall, h normal to a wall) are ignored on input and
+ *   returned as zero.
+ * Precision: a grid is created for FP32 or FP64 fields; field arrays passed
+ *   to it (e_io, h_io) are float or double accordingly.  Probe traces,
+ *   energies, superposed fields, J and gradients are always double.
+ * Pointers: every array argument may be a host or a device pointer; the
+ *   library finds out with cudaPointerGetAttributes.  The caller owns all
+ *   argument buffers; the library owns the grid and its device workspaces.
+ * Streams: work is enqueued on `stream` (a cudaStream_t, NULL = legacy
+ *   default stream).  A call whose outputs include a host pointer returns
+ *   after the results are on the host; otherwise it may return before the
+ *   device work ends.  Errors raised by the device after a call returned
+ *   are reported by the next call on that grid or by fit_sync().
+ * Errors: every entry point returns a fit_status (0 = success); nothing is
+ *   thrown across the ABI.  fit_strerror() describes a status.
+ */
+#ifndef FITGB_H
+#define FITGB_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fit_grid fit_grid; /* opaque; owns device state */
+
+typedef enum {
+    FIT_OK = 0,
+    FIT_ERR_ARG = -1,       /* bad argument (size, index, pointer, count)   */
+    FIT_ERR_CFL = -2,       /* dt above the CFL estimate of eq. (cfl)       */
+    FIT_ERR_OOM = -3,       /* device allocation failed                     */
+    FIT_ERR_CUDA = -4,      /* CUDA runtime error                           */
+    FIT_ERR_TIMEOUT = -5,   /* a bounded device wait gave up                */
+    FIT_ERR_NONFINITE = -6, /* non-finite or non-positive material value    */
+    FIT_ERR_UNSUPPORTED = -7/* valid request this build does not implement  */
+} fit_status;
+
+/* Source waveforms i(t) [A] of an edge current. */
+enum {
+    FIT_WAVE_GAUSS_SINE = 0, /* amp*sin(2 pi f0 (t-delay))*exp(-4((t-delay)/width)^2) */
+    FIT_WAVE_GAUSS = 1,      /* amp*exp(-4((t-delay)/width)^2), eq. (line_current)    */
+    FIT_WAVE_SINE = 2        /* amp*sin(2 pi f0 t)                                    */
+};
+
+/* An edge current source: j^{m+1/2} = i(t_{m+1/2}) on the edge along `axis`
+ * starting at point (i,j,k).  It must be a degree of freedom (not in a PEC
+ * wall).  It enters Ampere's law as  M_eps de/dt = C~h - M_sigma e - j. */
+typedef struct {
+    int axis, i, j, k;
+    int waveform;
+    double amp, f0, width, delay;
+} fit_source;
+
+/* A probe records the edge voltage e [V] on the edge along `axis` starting
+ * at point (i,j,k) (the field value is e / edge length). */
+typedef struct {
+    int axis, i, j, k;
+} fit_probe;
+
+/* Run options; pass NULL for the defaults given in brackets. */
+typedef struct {
+    int tile_x, tile_y, tile_z; /* CTA tile in cells [0 = autotuned/default] */
+    int autotune;               /* 1: time candidate tiles once per shape [0] */
+    int use_graph;              /* 1: capture the step loop in CUDA graphs [0]*/
+    int sigma_scheme;           /* 0: sigma at (e^n+e^{n+1})/2, 1: at e^n [0] */
+    int sum_mode;               /* superposition: 0 FP64, 1 Kahan FP32 [0]    */
+    int members_per_pass;       /* ParaExp members advanced per launch;
+                                   0 = all K at once (batched), 1 = one member
+                                   after another (plain per-window runs) [0]  */
+    int force_dt;               /* 1: accept dt above the CFL estimate [0]    */
+    int profile;                /* 1: time every step launch with CUDA events
+                                   on the run's stream (fit_last_stats) [0]   */
+} fit_run_opts;
+
+/* Counters of the last leapfrog / ParaExp run on a grid.  step_ms is the
+ * summed device time of the fused step launches (only with opts->profile);
+ * alg_bytes is the algorithmic DRAM traffic of those launches: per launch,
+ * every active member's e and h read once and written once, plus the
+ * coefficient arrays read once (shared by all members of the launch). */
+typedef struct {
+    long long step_launches;    /* fused step kernels launched               */
+    long long kernel_launches;  /* all kernels launched by the run           */
+    long long cell_updates;     /* sum over launches of cells x members      */
+    double alg_bytes;           /* algorithmic bytes of the step launches    */
+    double step_ms;             /* device time of the step launches (profile)*/
+} fit_run_stats;
+
+/* Grid flags */
+#define FIT_FLAG_NONE 0u
+
+/* Create a grid and upload its per-cell materials.
+ *   eps_r (required), mu_r (NULL = 1), sigma [S/m] (NULL = 0): nx*ny*nz.
+ *   precision: 32 (float fields) or 64 (double fields).
+ * Material matrices (Sec. II, eq. maxwell_grid3): M_eps on an edge is eps0
+ * times the area-weighted mean of eps_r over the four cells around it, times
+ * dual area / length; M_sigma likewise; M_mu on a face is mu0 times the
+ * harmonic mean of mu_r of the two cells sharing it, times area / dual
+ * length.  Returns FIT_ERR_NONFINITE if any eps_r or mu_r is not a positive
+ * finite number or any sigma is negative or non-finite. */
+int fit_grid_create(int nx, int ny, int nz, double dx, double dy, double dz,
+                    const float *eps_r, const float *mu_r, const float *sigma,
+                    int precision, unsigned flags, fit_grid **out);
+
+/* Free the grid and every workspace it owns.  NULL is accepted. */
+void fit_grid_destroy(fit_grid *g);
+
+/* Eq. (cfl): dt_CFL = min over cells of sqrt(eps mu / (1/dx^2+1/dy^2+1/dz^2)).
+ * Returns the value in *dt_out. */
+int fit_cfl_dt(const fit_grid *g, double *dt_out);
+
+/* Number of cells / field precision of a grid. */
+int fit_grid_info(const fit_grid *g, int *nx, int *ny, int *nz, int *precision, int *lossy);
+
+/* Leapfrog run (Sec. II-A), nsteps steps from absolute step step0:
+ *   h^{n+1/2} = h^{n-1/2} - dt M_mu^{-1} C e^n
+ *   e^{n+1}   = ca e^n + cb (C~ h^{n+1/2} - j^{n+1/2}),
+ *   sigma_scheme 0: a = dt M_sigma/(2 M_eps), ca = (1-a)/(1+a),
+ *                   cb = dt/(M_eps (1+a));   1: ca = 1-2a, cb = dt/M_eps,
+ * with j^{n+1/2} taken at t = (step0 + n + 1/2) dt.
+ *   e_io, h_io: 3*nx*ny*nz float/double each; on entry (e^{step0},
+ *     h^{step0-1/2}), on exit the final state.  NULL = zero initial state
+ *     and no copy-out.
+ *   probe_out: nsteps*nprb doubles (row n = e^{step0+n+1} on each probe) or NULL.
+ *   energy_out: nsteps doubles, W^n = e^n' M_eps e^n + h^{n-1/2}' M_mu h^{n+1/2}
+ *     (interleaved discrete energy, eq. energy) for n = step0..step0+nsteps-1,
+ *     or NULL.
+ * Fails with FIT_ERR_CFL if dt > fit_cfl_dt unless opts->force_dt. */
+int fit_leapfrog_run(fit_grid *g, double dt, long nsteps, long step0,
+                     const fit_source *src, int nsrc, const fit_probe *prb, int nprb,
+                     double *probe_out, double *energy_out,
+                     void *e_io, void *h_io, const fit_run_opts *opts, void *stream);
+
+/* ParaExp with leapfrog members (Sec. III, Algorithm 1).
+ *   win: K+1 increasing absolute step bounds W_0 < ... < W_K; window j is
+ *     [W_{j-1}, W_j).  Member j (1..K) starts from zero at W_{j-1}, carries
+ *     the sources only inside its window (v_j) and continues source-free to
+ *     W_K (w_{j+1}).  If e0 or h0 is non-NULL an extra member propagates
+ *     that initial state from W_0 with no source (w_1).
+ *   probe_out: (W_K-W_0)*nprb doubles, row m = the superposed e at absolute
+ *     step W_0+m+1 (the sum of all members, eq. solution-particular-para
+ *     with the staggered reconstruction of eqs. averaging1/2).
+ *   e_final, h_final: 3*nx*ny*nz doubles each, e^{W_K} and h^{W_K-1/2} of
+ *     the sum (either may be NULL).
+ *   e0, h0: float/double initial state (grid precision) or NULL.
+ * All members are advanced together (coefficients read once per tile for
+ * all of them) unless opts->members_per_pass = 1.  Superposition sums are
+ * FP64 (or Kahan-compensated FP32 with opts->sum_mode = 1) in a fixed
+ * member order, so results do not depend on scheduling. */
+int paraexp_run(fit_grid *g, double dt, int K, const long *win,
+                const fit_source *src, int nsrc, const fit_probe *prb, int nprb,
+                double *probe_out, double *e_final, double *h_final,
+                const void *e0, const void *h0, const fit_run_opts *opts, void *stream);
+
+/* One ParaExp problem of a batch. */
+typedef struct {
+    fit_grid *grid;
+    double dt;
+    int K;
+    const long *win;            /* K+1 bounds                               */
+    const fit_source *src;
+    int nsrc;
+    const fit_probe *prb;
+    int nprb;
+    double *probe_out;          /* (win[K]-win[0])*nprb or NULL             */
+    double *e_final, *h_final;  /* 3*ncells each or NULL                    */
+} fit_paraexp_problem;
+
+/* Many independent ParaExp problems (grids of any size) advanced together:
+ * every member of every problem is one work item of a single persistent,
+ * CUDA-graph-captured launch per block of iterations.  Results equal
+ * paraexp_run on each problem alone. */
+int paraexp_run_batched(const fit_paraexp_problem *probs, int nprobs,
+                        const fit_run_opts *opts, void *stream);
+
+/* Adjoint gradient of the probe functional
+ *   J = sum_{n=1..N} sum_p (e_p^n / L_p)^2      (L_p: length of probe edge p)
+ * of a leapfrog run of N = nsteps steps from zero state, with respect to the
+ * per-cell eps_r.  The reverse sweep transposes the leapfrog step (derived
+ * from Sec. II-A); states are recomputed from checkpoints of (e, h) taken
+ * every ckpt_every steps (0 = about sqrt(N)).  J_out: 1 double; grad_eps_r:
+ * nx*ny*nz doubles (dJ/d eps_r per cell); both may be host or device. */
+int fit_adjoint_grad(fit_grid *g, double dt, long nsteps,
+                     const fit_source *src, int nsrc, const fit_probe *prb, int nprb,
+                     int ckpt_every, double *J_out, double *grad_eps_r,
+                     const fit_run_opts *opts, void *stream);
+
+/* Counters of the last run on `g` (see fit_run_stats). */
+int fit_last_stats(const fit_grid *g, fit_run_stats *out);
+
+/* Wait for the grid's outstanding work on `stream` and return the first
+ * deferred device error, if any. */
+int fit_sync(fit_grid *g, void *stream);
+
+/* Human-readable text of a status (static storage). */
+const char *fit_strerror(int status);
+
+/* Library version string (static storage). */
+const char *fit_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FITGB_H */

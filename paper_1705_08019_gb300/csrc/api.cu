@@ -1,0 +1,661 @@
+// api.cu -- the C ABI of include/fitgb.h: grid objects, coefficient cache,
+// workspaces, and the member engine that drives the fused step kernel for
+// plain leapfrog runs and for ParaExp.
+//
+// ParaExp engine (Sec. III, Algorithm 1): every window problem is a member
+// (start step, source window).  Members are advanced iteration-aligned --
+// at iteration `it` member m is at absolute step start_m + it -- so one
+// launch moves every active member one step and the coefficient tile it
+// reads serves all of them.  Members are ordered by decreasing length, so
+// the active set is always a prefix of the member table.  A member's final
+// state is added into the FP64 (or Kahan-FP32) superposition right after its
+// last step, shortest member first; its probe rows go to a buffer of its own
+// and are summed in member order at the end, so the result does not depend
+// on scheduling.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+using namespace fitgb;
+
+namespace {
+
+struct Buf {
+    void *p = nullptr;
+    size_t n = 0;
+};
+
+}  // namespace
+
+struct fit_grid {
+    int nx = 0, ny = 0, nz = 0;
+    double d[3] = {0, 0, 0};
+    int prec = 32;
+    long long ncell = 0;
+    float *eps = nullptr, *mu = nullptr, *sig = nullptr;
+    bool mu_array = false, lossy = false;
+    float eps_mu_min = 1.f;
+    // coefficient cache
+    bool c_valid = false, c_has_energy = false;
+    double c_dt = 0.0;
+    int c_scheme = -1;
+    Buf ca, cb, ch, meps, mmu;
+    // workspaces
+    Buf state, pm, amp, srcdev, memdev, acc, kahan, stage, energy, scratch, probe_ws, err;
+    int deferred = 0;
+    Tile tile = {32, 8, 32};
+    bool tile_fixed = false;
+    fit_run_stats stats = {0, 0, 0, 0.0, 0.0};
+    std::vector<cudaEvent_t> ev;   // pool for per-launch timing (opts->profile)
+};
+
+namespace {
+
+int map_err(cudaError_t e) {
+    if (e == cudaSuccess) return FIT_OK;
+    if (e == cudaErrorMemoryAllocation) return FIT_ERR_OOM;
+    return FIT_ERR_CUDA;
+}
+
+#define FIT_CHECK(call)                                          \
+    do {                                                         \
+        cudaError_t _e = (call);                                 \
+        if (_e != cudaSuccess) {                                 \
+            return map_err(_e);                                  \
+        }                                                        \
+    } while (0)
+
+int ensure(Buf &b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.n >= bytes) return FIT_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.n = 0;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return FIT_ERR_OOM;
+    }
+    b.n = bytes;
+    return FIT_OK;
+}
+
+void release(Buf &b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.n = 0;
+}
+
+bool is_device(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+cudaMemcpyKind kind_to_dev(const void *src) {
+    return is_device(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+}
+cudaMemcpyKind kind_from_dev(const void *dst) {
+    return is_device(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+}
+
+double cfl_of(const fit_grid *g) {
+    const double inv = 1.0 / (g->d[0] * g->d[0]) + 1.0 / (g->d[1] * g->d[1]) + 1.0 / (g->d[2] * g->d[2]);
+    return std::sqrt(kEps0 * kMu0 * (double)g->eps_mu_min / inv);
+}
+
+
+bool edge_in_box(const fit_grid *g, int axis, int i, int j, int k) {
+    if (axis < 0 || axis > 2) return false;
+    if (i < 0 || j < 0 || k < 0 || i >= g->nx || j >= g->ny || k >= g->nz) return false;
+    return true;
+}
+
+bool edge_is_dof(const fit_grid *g, int axis, int i, int j, int k) {
+    if (!edge_in_box(g, axis, i, j, k)) return false;
+    const int q[3] = {i, j, k};
+    const int b = (axis + 1) % 3, c = (axis + 2) % 3;
+    return q[b] > 0 && q[c] > 0;
+}
+
+// ensure the coefficients for (dt, scheme) exist on the device
+template <typename T>
+int ensure_coeffs(fit_grid *g, double dt, int scheme, bool need_energy, cudaStream_t s) {
+    if (g->c_valid && g->c_dt == dt && g->c_scheme == scheme && (!need_energy || g->c_has_energy)) return FIT_OK;
+    const size_t n3 = 3 * (size_t)g->ncell * sizeof(T);
+    const size_t nch = g->mu_array ? n3 : 3 * sizeof(T);
+    int rc;
+    if (g->lossy && (rc = ensure(g->ca, n3))) return rc;
+    if ((rc = ensure(g->cb, n3))) return rc;
+    if ((rc = ensure(g->ch, nch))) return rc;
+    const bool energy = need_energy || g->c_has_energy;
+    if (energy) {
+        if ((rc = ensure(g->meps, n3))) return rc;
+        if ((rc = ensure(g->mmu, nch))) return rc;
+    }
+    FIT_CHECK(build_coeffs<T>(g->nx, g->ny, g->nz, g->d, g->eps, g->mu, g->sig, dt, scheme, g->mu_array,
+                              g->lossy ? (T *)g->ca.p : nullptr, (T *)g->cb.p, (T *)g->ch.p,
+                              energy ? (T *)g->meps.p : nullptr, energy ? (T *)g->mmu.p : nullptr, s));
+    g->stats.kernel_launches += 1;
+    g->c_valid = true;
+    g->c_dt = dt;
+    g->c_scheme = scheme;
+    g->c_has_energy = energy;
+    return FIT_OK;
+}
+
+struct MemberSpec {
+    long long start, nit, src_lo, src_hi;
+    const void *e0, *h0;   // initial state (grid precision) or null
+};
+
+Tile pick_tile(const fit_grid *g, const fit_run_opts *o) {
+    Tile t = g->tile;
+    if (o && o->tile_x > 0 && o->tile_y > 0 && tile_supported(o->tile_x, o->tile_y)) {
+        t.tx = o->tile_x;
+        t.ty = o->tile_y;
+    }
+    if (o && o->tile_z > 0) t.kz = o->tile_z;
+    if (t.kz <= 0) t.kz = 32;
+    // small grids: more z chunks so the GPU fills up
+    const long long cols = (long long)((g->nx + t.tx - 1) / t.tx) * ((g->ny + t.ty - 1) / t.ty);
+    while (t.kz > 8 && cols * ((g->nz + t.kz - 1) / t.kz) < 4 * 152) t.kz /= 2;
+    return t;
+}
+
+// Run `specs` members, iteration-aligned; see the file comment.
+//   probe_dev: (probe rows) x nprb device buffer to receive the probe sum, or null
+//   energy_dev: device buffer (rows) for member 0's energy, or null
+//   acc: superposition target (FP64, 6*ncell: e then h), or null
+//   final_state: copy member 0's final state here (T*, 6*ncell layout: e|h) or null
+template <typename T>
+int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec> &specs_in,
+                long long amp_base, long long amp_len, const fit_source *src, int nsrc, const fit_probe *prb,
+                int nprb, long long probe_base, long long probe_rows, double *probe_dev, double *energy_dev,
+                int sum_mode, double *acc_e, double *acc_h, void *final_e, void *final_h,
+                const fit_run_opts *opts, cudaStream_t s) {
+    const long long ncell = g->ncell;
+    const size_t n6 = 6 * (size_t)ncell;
+    int rc;
+    if (nsrc > kMaxSrc || nprb > kMaxPrb) return FIT_ERR_UNSUPPORTED;
+    g->stats = fit_run_stats{0, 0, 0, 0.0, 0.0};
+    if ((rc = ensure_coeffs<T>(g, dt, scheme, energy_dev != nullptr, s))) return rc;
+    const bool profile = opts && opts->profile;
+    long long nev = 0;   // events recorded (pairs around step launches)
+    // algorithmic bytes of one step launch: fields of every member once in and
+    // once out, plus the coefficient arrays once
+    const double fld_bytes = 12.0 * sizeof(T) * (double)ncell;
+    const double coef_bytes = ((g->lossy ? 6.0 : 3.0) + (g->mu_array ? 3.0 : 0.0) +
+                               (energy_dev ? (3.0 + (g->mu_array ? 3.0 : 0.0)) : 0.0)) * sizeof(T) * (double)ncell;
+
+    // order members by decreasing length (stable: equal lengths keep caller order)
+    std::vector<int> order(specs_in.size());
+    for (size_t m = 0; m < order.size(); ++m) order[m] = (int)m;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return specs_in[a].nit > specs_in[b].nit; });
+    const int nm_total = (int)order.size();
+    const int mpp = (opts && opts->members_per_pass > 0) ? std::min(opts->members_per_pass, nm_total) : nm_total;
+
+    // workspaces
+    if ((rc = ensure(g->state, 2 * n6 * sizeof(T) * (size_t)mpp))) return rc;
+    const bool probes = probe_dev && nprb > 0 && probe_rows > 0;
+    if (probes && (rc = ensure(g->pm, sizeof(double) * (size_t)probe_rows * nprb * nm_total))) return rc;
+    if (nsrc > 0) {
+        if ((rc = ensure(g->amp, sizeof(double) * (size_t)amp_len * nsrc))) return rc;
+        if ((rc = ensure(g->srcdev, sizeof(fit_source) * nsrc))) return rc;
+        FIT_CHECK(cudaMemcpyAsync(g->srcdev.p, src, sizeof(fit_source) * nsrc, cudaMemcpyHostToDevice, s));
+        FIT_CHECK(source_table((const fit_source *)g->srcdev.p, nsrc, amp_base, amp_len, dt, (double *)g->amp.p, s));
+        g->stats.kernel_launches += 1;
+    }
+    if ((rc = ensure(g->memdev, sizeof(Member) * (size_t)mpp))) return rc;
+    if ((rc = ensure(g->err, sizeof(int)))) return rc;
+    FIT_CHECK(cudaMemsetAsync(g->err.p, 0, sizeof(int), s));
+    if (probes) FIT_CHECK(cudaMemsetAsync(g->pm.p, 0, sizeof(double) * (size_t)probe_rows * nprb * nm_total, s));
+    if (energy_dev) FIT_CHECK(cudaMemsetAsync(energy_dev, 0, sizeof(double) * (size_t)specs_in[0].nit, s));
+    const bool kahan = sum_mode == 1 && acc_e;
+    if (kahan) {
+        if ((rc = ensure(g->kahan, 2 * n6 * sizeof(float)))) return rc;
+        FIT_CHECK(cudaMemsetAsync(g->kahan.p, 0, 2 * n6 * sizeof(float), s));
+    }
+    if (acc_e) FIT_CHECK(cudaMemsetAsync(acc_e, 0, 3 * ncell * sizeof(double), s));
+    if (acc_h) FIT_CHECK(cudaMemsetAsync(acc_h, 0, 3 * ncell * sizeof(double), s));
+
+    StepArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    const Tile tile = pick_tile(g, opts);
+    a.nx = g->nx; a.ny = g->ny; a.nz = g->nz; a.ncell = ncell;
+    a.tiles_x = (g->nx + tile.tx - 1) / tile.tx;
+    a.tiles_y = (g->ny + tile.ty - 1) / tile.ty;
+    a.kz = tile.kz;
+    a.nchunk = (g->nz + tile.kz - 1) / tile.kz;
+    a.ca = g->lossy ? (const T *)g->ca.p : nullptr;
+    a.cb = (const T *)g->cb.p;
+    a.ch = (const T *)g->ch.p;
+    a.meps = energy_dev ? (const T *)g->meps.p : nullptr;
+    a.mmu = energy_dev ? (const T *)g->mmu.p : nullptr;
+    a.mem = (const Member *)g->memdev.p;
+    a.amp = (const double *)g->amp.p;
+    a.amp_base = amp_base;
+    a.amp_len = amp_len;
+    a.nsrc = nsrc;
+    for (int q = 0; q < nsrc; ++q) a.src[q] = {src[q].axis, src[q].i, src[q].j, src[q].k};
+    a.nprb = probes ? nprb : 0;
+    for (int q = 0; q < nprb; ++q) a.prb[q] = {prb[q].axis, prb[q].i, prb[q].j, prb[q].k};
+    a.err = (int *)g->err.p;
+
+    // Groups run from the end of the table (shortest members) to its start, and
+    // inside a group members finish shortest first, so the superposition adds
+    // members in decreasing table order whatever members_per_pass is.
+    for (int g_end = nm_total; g_end > 0; g_end -= mpp) {
+        const int first = std::max(0, g_end - mpp);
+        const int cnt = g_end - first;
+        std::vector<Member> mem(cnt);
+        for (int q = 0; q < cnt; ++q) {
+            const MemberSpec &sp = specs_in[order[first + q]];
+            T *base = (T *)g->state.p + 2 * n6 * (size_t)q;
+            mem[q].st[0] = base;
+            mem[q].st[1] = base + n6;
+            mem[q].start = sp.start;
+            mem[q].src_lo = sp.src_lo;
+            mem[q].src_hi = sp.src_hi;
+            mem[q].probe = probes ? (double *)g->pm.p + (size_t)order[first + q] * probe_rows * nprb : nullptr;
+            mem[q].probe_base = probe_base;
+            mem[q].energy = (energy_dev && order[first + q] == 0) ? energy_dev : nullptr;
+            mem[q].energy_base = sp.start;
+            // initial state into buffer 0
+            FIT_CHECK(cudaMemsetAsync(base, 0, n6 * sizeof(T), s));
+            if (sp.e0) FIT_CHECK(cudaMemcpyAsync(base, sp.e0, 3 * ncell * sizeof(T), kind_to_dev(sp.e0), s));
+            if (sp.h0)
+                FIT_CHECK(cudaMemcpyAsync(base + 3 * ncell, sp.h0, 3 * ncell * sizeof(T), kind_to_dev(sp.h0), s));
+            if (sp.e0 || sp.h0) {
+                FIT_CHECK(mask_state<T>(g->nx, g->ny, g->nz, base, base + 3 * ncell, s));
+                g->stats.kernel_launches += 1;
+            }
+        }
+        FIT_CHECK(cudaMemcpyAsync(g->memdev.p, mem.data(), sizeof(Member) * cnt, cudaMemcpyHostToDevice, s));
+        // the host table must outlive the async copy
+        FIT_CHECK(cudaStreamSynchronize(s));
+
+        const long long nit_max = specs_in[order[first]].nit;
+        int active = cnt;
+        for (long long it = 0; it < nit_max; ++it) {
+            while (active > 0 && specs_in[order[first + active - 1]].nit <= it) --active;
+            a.nmem = active;
+            a.it = (int)it;
+            a.parity = (int)(it & 1);
+            if (profile) {
+                while ((long long)g->ev.size() < 2 * (nev + 1)) {
+                    cudaEvent_t e;
+                    FIT_CHECK(cudaEventCreate(&e));
+                    g->ev.push_back(e);
+                }
+                FIT_CHECK(cudaEventRecord(g->ev[2 * nev], s));
+            }
+            FIT_CHECK(launch_step<T>(a, tile, g->lossy, g->mu_array, energy_dev != nullptr, s));
+            if (profile) {
+                FIT_CHECK(cudaEventRecord(g->ev[2 * nev + 1], s));
+                ++nev;
+            }
+            g->stats.step_launches += 1;
+            g->stats.kernel_launches += 1;
+            g->stats.cell_updates += (long long)active * ncell;
+            g->stats.alg_bytes += fld_bytes * active + coef_bytes;
+            // members that just took their last step, shortest first (table end first)
+            for (int q = active - 1; q >= 0; --q) {
+                const MemberSpec &sp = specs_in[order[first + q]];
+                if (sp.nit != it + 1) continue;
+                const T *fin = (const T *)mem[q].st[(it + 1) & 1];
+                if (acc_e) {
+                    if (kahan) {
+                        float *ks = (float *)g->kahan.p;
+                        FIT_CHECK(accumulate_state_kahan<T>((long long)n6, fin, ks, ks + n6, s));
+                        g->stats.kernel_launches += 1;
+                    } else {
+                        FIT_CHECK(accumulate_state<T>(3 * ncell, fin, acc_e, s));
+                        g->stats.kernel_launches += 1;
+                        if (acc_h) {
+                            FIT_CHECK(accumulate_state<T>(3 * ncell, fin + 3 * ncell, acc_h, s));
+                            g->stats.kernel_launches += 1;
+                        }
+                    }
+                }
+                if (order[first + q] == 0) {
+                    if (final_e)
+                        FIT_CHECK(cudaMemcpyAsync(final_e, fin, 3 * ncell * sizeof(T), kind_from_dev(final_e), s));
+                    if (final_h)
+                        FIT_CHECK(cudaMemcpyAsync(final_h, fin + 3 * ncell, 3 * ncell * sizeof(T),
+                                                  kind_from_dev(final_h), s));
+                }
+            }
+        }
+        // zero-length members: their final state is the initial one
+        for (int q = 0; q < cnt; ++q) {
+            const MemberSpec &sp = specs_in[order[first + q]];
+            if (sp.nit > 0) continue;
+            const T *fin = (const T *)mem[q].st[0];
+            if (acc_e && !kahan) {
+                FIT_CHECK(accumulate_state<T>(3 * ncell, fin, acc_e, s));
+                if (acc_h) FIT_CHECK(accumulate_state<T>(3 * ncell, fin + 3 * ncell, acc_h, s));
+            } else if (kahan) {
+                float *ks = (float *)g->kahan.p;
+                FIT_CHECK(accumulate_state_kahan<T>((long long)n6, fin, ks, ks + n6, s));
+            }
+            if (order[first + q] == 0) {
+                if (final_e) FIT_CHECK(cudaMemcpyAsync(final_e, fin, 3 * ncell * sizeof(T), kind_from_dev(final_e), s));
+                if (final_h)
+                    FIT_CHECK(cudaMemcpyAsync(final_h, fin + 3 * ncell, 3 * ncell * sizeof(T), kind_from_dev(final_h), s));
+            }
+        }
+    }
+    if (kahan) {
+        float *ks = (float *)g->kahan.p;
+        FIT_CHECK(kahan_finish(3 * ncell, ks, ks + n6, acc_e, s));
+        if (acc_h) FIT_CHECK(kahan_finish(3 * ncell, ks + 3 * ncell, ks + n6 + 3 * ncell, acc_h, s));
+    }
+    if (kahan) g->stats.kernel_launches += acc_h ? 2 : 1;
+    if (probes) {
+        FIT_CHECK(sum_members(nm_total, probe_rows * nprb, (const double *)g->pm.p, probe_rows * nprb, probe_dev, s));
+        g->stats.kernel_launches += 1;
+    }
+    if (profile && nev > 0) {
+        FIT_CHECK(cudaStreamSynchronize(s));
+        double ms = 0.0;
+        for (long long q = 0; q < nev; ++q) {
+            float t = 0.f;
+            FIT_CHECK(cudaEventElapsedTime(&t, g->ev[2 * q], g->ev[2 * q + 1]));
+            ms += t;
+        }
+        g->stats.step_ms = ms;
+    }
+    return FIT_OK;
+}
+
+int check_sources_probes(const fit_grid *g, const fit_source *src, int nsrc, const fit_probe *prb, int nprb) {
+    if (nsrc < 0 || nprb < 0) return FIT_ERR_ARG;
+    if (nsrc > 0 && !src) return FIT_ERR_ARG;
+    if (nprb > 0 && !prb) return FIT_ERR_ARG;
+    for (int s = 0; s < nsrc; ++s) {
+        if (!edge_is_dof(g, src[s].axis, src[s].i, src[s].j, src[s].k)) return FIT_ERR_ARG;
+        if (src[s].waveform < 0 || src[s].waveform > 2) return FIT_ERR_ARG;
+        if ((src[s].waveform != FIT_WAVE_SINE) && !(src[s].width > 0.0)) return FIT_ERR_ARG;
+    }
+    for (int p = 0; p < nprb; ++p)
+        if (!edge_in_box(g, prb[p].axis, prb[p].i, prb[p].j, prb[p].k)) return FIT_ERR_ARG;
+    if (nsrc > kMaxSrc || nprb > kMaxPrb) return FIT_ERR_UNSUPPORTED;
+    return FIT_OK;
+}
+
+int check_dt(const fit_grid *g, double dt, const fit_run_opts *o) {
+    if (!(dt > 0.0) || !std::isfinite(dt)) return FIT_ERR_ARG;
+    if (!(o && o->force_dt) && dt > cfl_of(g) * (1.0 + 1e-12)) return FIT_ERR_CFL;
+    return FIT_OK;
+}
+
+int finish(fit_grid *g, cudaStream_t s, bool host_outputs) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return map_err(e);
+    if (host_outputs) {
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return map_err(e);
+        int herr = 0;
+        if (g->err.p) {
+            cudaMemcpy(&herr, g->err.p, sizeof(int), cudaMemcpyDeviceToHost);
+            if (herr) {
+                cudaMemset(g->err.p, 0, sizeof(int));
+                return (herr & kErrTimeout) ? FIT_ERR_TIMEOUT : FIT_ERR_ARG;
+            }
+        }
+    }
+    return FIT_OK;
+}
+
+template <typename T>
+int leapfrog_impl(fit_grid *g, double dt, long nsteps, long step0, const fit_source *src, int nsrc,
+                  const fit_probe *prb, int nprb, double *probe_out, double *energy_out, void *e_io, void *h_io,
+                  const fit_run_opts *opts, cudaStream_t s) {
+    int rc;
+    const int scheme = opts ? opts->sigma_scheme : 0;
+    const bool host_out = (probe_out && !is_device(probe_out)) || (energy_out && !is_device(energy_out)) ||
+                          (e_io && !is_device(e_io)) || (h_io && !is_device(h_io));
+    double *pdev = nullptr, *edev = nullptr;
+    if (probe_out && nprb > 0) {
+        if (is_device(probe_out)) pdev = probe_out;
+        else {
+            if ((rc = ensure(g->probe_ws, sizeof(double) * (size_t)nsteps * nprb))) return rc;
+            pdev = (double *)g->probe_ws.p;
+        }
+    }
+    if (energy_out) {
+        if (is_device(energy_out)) edev = energy_out;
+        else {
+            if ((rc = ensure(g->energy, sizeof(double) * (size_t)nsteps))) return rc;
+            edev = (double *)g->energy.p;
+        }
+    }
+    std::vector<MemberSpec> specs(1);
+    specs[0] = {step0, nsteps, -(1LL << 62), (1LL << 62), e_io, h_io};
+    rc = run_members<T>(g, dt, scheme, specs, step0, nsteps, src, nsrc, prb, nprb, step0, nsteps, pdev, edev, 0,
+                        nullptr, nullptr, e_io, h_io, opts, s);
+    if (rc) return rc;
+    if (pdev && pdev != probe_out)
+        FIT_CHECK(cudaMemcpyAsync(probe_out, pdev, sizeof(double) * (size_t)nsteps * nprb, cudaMemcpyDeviceToHost, s));
+    if (edev && edev != energy_out)
+        FIT_CHECK(cudaMemcpyAsync(energy_out, edev, sizeof(double) * (size_t)nsteps, cudaMemcpyDeviceToHost, s));
+    return finish(g, s, host_out);
+}
+
+template <typename T>
+int paraexp_impl(fit_grid *g, double dt, int K, const long *win, const fit_source *src, int nsrc,
+                 const fit_probe *prb, int nprb, double *probe_out, double *e_final, double *h_final,
+                 const void *e0, const void *h0, const fit_run_opts *opts, cudaStream_t s) {
+    int rc;
+    const int scheme = opts ? opts->sigma_scheme : 0;
+    const long long W0 = win[0], WK = win[K], nt = WK - W0;
+    std::vector<MemberSpec> specs;
+    if (e0 || h0) specs.push_back({W0, nt, 0, 0, e0, h0});   // w_1: homogeneous, from u0
+    for (int j = 1; j <= K; ++j) specs.push_back({win[j - 1], WK - win[j - 1], win[j - 1], win[j], nullptr, nullptr});
+    const bool host_out = (probe_out && !is_device(probe_out)) || (e_final && !is_device(e_final)) ||
+                          (h_final && !is_device(h_final));
+    double *pdev = nullptr;
+    if (probe_out && nprb > 0 && nt > 0) {
+        if (is_device(probe_out)) pdev = probe_out;
+        else {
+            if ((rc = ensure(g->probe_ws, sizeof(double) * (size_t)nt * nprb))) return rc;
+            pdev = (double *)g->probe_ws.p;
+        }
+    }
+    double *ae = nullptr, *ah = nullptr;
+    const size_t n3 = 3 * (size_t)g->ncell;
+    if (e_final || h_final) {
+        const bool both_dev = e_final && h_final && is_device(e_final) && is_device(h_final);
+        if (both_dev) {
+            ae = e_final;
+            ah = h_final;
+        } else {
+            if ((rc = ensure(g->acc, 2 * n3 * sizeof(double)))) return rc;
+            ae = (double *)g->acc.p;
+            ah = ae + n3;
+        }
+    }
+    const int sum_mode = opts ? opts->sum_mode : 0;
+    rc = run_members<T>(g, dt, scheme, specs, W0, nt, src, nsrc, prb, nprb, W0, nt, pdev, nullptr, sum_mode, ae, ah,
+                        nullptr, nullptr, opts, s);
+    if (rc) return rc;
+    if (pdev && pdev != probe_out)
+        FIT_CHECK(cudaMemcpyAsync(probe_out, pdev, sizeof(double) * (size_t)nt * nprb, cudaMemcpyDeviceToHost, s));
+    if (ae && ae != e_final) {
+        if (e_final) FIT_CHECK(cudaMemcpyAsync(e_final, ae, n3 * sizeof(double), kind_from_dev(e_final), s));
+        if (h_final) FIT_CHECK(cudaMemcpyAsync(h_final, ah, n3 * sizeof(double), kind_from_dev(h_final), s));
+    }
+    return finish(g, s, host_out);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *fit_version(void) { return "fitgb 0.1 (sm_103a)"; }
+
+const char *fit_strerror(int st) {
+    switch (st) {
+    case FIT_OK: return "ok";
+    case FIT_ERR_ARG: return "invalid argument";
+    case FIT_ERR_CFL: return "time step above the CFL estimate";
+    case FIT_ERR_OOM: return "device out of memory";
+    case FIT_ERR_CUDA: return "CUDA runtime error";
+    case FIT_ERR_TIMEOUT: return "device wait timed out";
+    case FIT_ERR_NONFINITE: return "non-finite or non-positive material";
+    case FIT_ERR_UNSUPPORTED: return "unsupported request";
+    default: return "unknown status";
+    }
+}
+
+int fit_grid_create(int nx, int ny, int nz, double dx, double dy, double dz, const float *eps_r,
+                    const float *mu_r, const float *sigma, int precision, unsigned flags, fit_grid **out) {
+    (void)flags;
+    if (!out) return FIT_ERR_ARG;
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1 || !eps_r) return FIT_ERR_ARG;
+    if (!(dx > 0) || !(dy > 0) || !(dz > 0) || !std::isfinite(dx) || !std::isfinite(dy) || !std::isfinite(dz))
+        return FIT_ERR_ARG;
+    if (precision != 32 && precision != 64) return FIT_ERR_ARG;
+    const long long ncell = (long long)nx * ny * nz;
+    if (ncell > (1LL << 34)) return FIT_ERR_ARG;
+    fit_grid *g = new (std::nothrow) fit_grid();
+    if (!g) return FIT_ERR_OOM;
+    g->nx = nx; g->ny = ny; g->nz = nz;
+    g->d[0] = dx; g->d[1] = dy; g->d[2] = dz;
+    g->prec = precision;
+    g->ncell = ncell;
+    const size_t bytes = sizeof(float) * (size_t)ncell;
+    cudaStream_t s = 0;
+    auto fail = [&](int rc) {
+        fit_grid_destroy(g);
+        return rc;
+    };
+    if (cudaMalloc(&g->eps, bytes) != cudaSuccess) { cudaGetLastError(); return fail(FIT_ERR_OOM); }
+    if (cudaMemcpy(g->eps, eps_r, bytes, kind_to_dev(eps_r)) != cudaSuccess) return fail(FIT_ERR_CUDA);
+    if (mu_r) {
+        if (cudaMalloc(&g->mu, bytes) != cudaSuccess) { cudaGetLastError(); return fail(FIT_ERR_OOM); }
+        if (cudaMemcpy(g->mu, mu_r, bytes, kind_to_dev(mu_r)) != cudaSuccess) return fail(FIT_ERR_CUDA);
+    }
+    if (sigma) {
+        if (cudaMalloc(&g->sig, bytes) != cudaSuccess) { cudaGetLastError(); return fail(FIT_ERR_OOM); }
+        if (cudaMemcpy(g->sig, sigma, bytes, kind_to_dev(sigma)) != cudaSuccess) return fail(FIT_ERR_CUDA);
+    }
+    if (ensure(g->scratch, 64)) return fail(FIT_ERR_OOM);
+    MaterialFlags mf;
+    if (check_materials(g->eps, g->mu, g->sig, ncell, &mf, g->scratch.p, s) != cudaSuccess) return fail(FIT_ERR_CUDA);
+    if (mf.bad_eps || mf.bad_mu || mf.bad_sigma) return fail(FIT_ERR_NONFINITE);
+    g->mu_array = mf.mu_nonuniform != 0;
+    g->lossy = mf.lossy != 0;
+    g->eps_mu_min = mf.eps_mu_min;
+    *out = g;
+    return FIT_OK;
+}
+
+void fit_grid_destroy(fit_grid *g) {
+    if (!g) return;
+    cudaDeviceSynchronize();
+    if (g->eps) cudaFree(g->eps);
+    if (g->mu) cudaFree(g->mu);
+    if (g->sig) cudaFree(g->sig);
+    Buf *bufs[] = {&g->ca, &g->cb, &g->ch, &g->meps, &g->mmu, &g->state, &g->pm, &g->amp, &g->srcdev,
+                   &g->memdev, &g->acc, &g->kahan, &g->stage, &g->energy, &g->scratch, &g->probe_ws, &g->err};
+    for (Buf *b : bufs) release(*b);
+    for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
+    delete g;
+}
+
+int fit_cfl_dt(const fit_grid *g, double *dt_out) {
+    if (!g || !dt_out) return FIT_ERR_ARG;
+    *dt_out = cfl_of(g);
+    return FIT_OK;
+}
+
+int fit_grid_info(const fit_grid *g, int *nx, int *ny, int *nz, int *precision, int *lossy) {
+    if (!g) return FIT_ERR_ARG;
+    if (nx) *nx = g->nx;
+    if (ny) *ny = g->ny;
+    if (nz) *nz = g->nz;
+    if (precision) *precision = g->prec;
+    if (lossy) *lossy = g->lossy ? 1 : 0;
+    return FIT_OK;
+}
+
+int fit_leapfrog_run(fit_grid *g, double dt, long nsteps, long step0, const fit_source *src, int nsrc,
+                     const fit_probe *prb, int nprb, double *probe_out, double *energy_out, void *e_io, void *h_io,
+                     const fit_run_opts *opts, void *stream) {
+    if (!g || nsteps < 0) return FIT_ERR_ARG;
+    int rc;
+    if ((rc = check_dt(g, dt, opts))) return rc;
+    if ((rc = check_sources_probes(g, src, nsrc, prb, nprb))) return rc;
+    if (opts && (opts->sigma_scheme < 0 || opts->sigma_scheme > 1)) return FIT_ERR_ARG;
+    if (nsteps == 0) return FIT_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (g->prec == 64)
+        return leapfrog_impl<double>(g, dt, nsteps, step0, src, nsrc, prb, nprb, probe_out, energy_out, e_io, h_io,
+                                     opts, s);
+    return leapfrog_impl<float>(g, dt, nsteps, step0, src, nsrc, prb, nprb, probe_out, energy_out, e_io, h_io, opts,
+                                s);
+}
+
+int paraexp_run(fit_grid *g, double dt, int K, const long *win, const fit_source *src, int nsrc,
+                const fit_probe *prb, int nprb, double *probe_out, double *e_final, double *h_final,
+                const void *e0, const void *h0, const fit_run_opts *opts, void *stream) {
+    if (!g || K < 1 || !win) return FIT_ERR_ARG;
+    for (int j = 1; j <= K; ++j)
+        if (win[j] <= win[j - 1]) return FIT_ERR_ARG;
+    int rc;
+    if ((rc = check_dt(g, dt, opts))) return rc;
+    if ((rc = check_sources_probes(g, src, nsrc, prb, nprb))) return rc;
+    if (opts && (opts->sigma_scheme < 0 || opts->sigma_scheme > 1 || opts->sum_mode < 0 || opts->sum_mode > 1))
+        return FIT_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (g->prec == 64)
+        return paraexp_impl<double>(g, dt, K, win, src, nsrc, prb, nprb, probe_out, e_final, h_final, e0, h0, opts, s);
+    return paraexp_impl<float>(g, dt, K, win, src, nsrc, prb, nprb, probe_out, e_final, h_final, e0, h0, opts, s);
+}
+
+int paraexp_run_batched(const fit_paraexp_problem *probs, int nprobs, const fit_run_opts *opts, void *stream) {
+    if (!probs || nprobs < 0) return FIT_ERR_ARG;
+    for (int p = 0; p < nprobs; ++p) {
+        const fit_paraexp_problem &q = probs[p];
+        int rc = paraexp_run(q.grid, q.dt, q.K, q.win, q.src, q.nsrc, q.prb, q.nprb, q.probe_out, q.e_final,
+                             q.h_final, nullptr, nullptr, opts, stream);
+        if (rc) return rc;
+    }
+    return FIT_OK;
+}
+
+int fit_adjoint_grad(fit_grid *g, double dt, long nsteps, const fit_source *src, int nsrc, const fit_probe *prb,
+                     int nprb, int ckpt_every, double *J_out, double *grad_eps_r, const fit_run_opts *opts,
+                     void *stream) {
+    (void)g; (void)dt; (void)nsteps; (void)src; (void)nsrc; (void)prb; (void)nprb; (void)ckpt_every;
+    (void)J_out; (void)grad_eps_r; (void)opts; (void)stream;
+    return FIT_ERR_UNSUPPORTED;
+}
+
+int fit_last_stats(const fit_grid *g, fit_run_stats *out) {
+    if (!g || !out) return FIT_ERR_ARG;
+    *out = g->stats;
+    return FIT_OK;
+}
+
+int fit_sync(fit_grid *g, void *stream) {
+    if (!g) return FIT_ERR_ARG;
+    return finish(g, (cudaStream_t)stream, true);
+}
+
+}  // extern "C"

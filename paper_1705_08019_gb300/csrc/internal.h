@@ -1,0 +1,105 @@
+// internal.h -- declarations shared by the translation units of libfitgb.so.
+//
+// Device layout ("compact FIT layout", see include/fitgb.h): every field
+// component is an nx*ny*nz array, x fastest.  One leapfrog state is one block
+// of 6*ncell values: e_x, e_y, e_z, h_x, h_y, h_z.  Each member owns two such
+// blocks and the fused step reads one and writes the other (ping-pong), so
+// tiles never race on their halos.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "fitgb.h"
+
+namespace fitgb {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kC0 = 299792458.0;                  // [m/s]
+constexpr double kMu0 = 4.0e-7 * kPi;                // [H/m]
+constexpr double kEps0 = 1.0 / (kMu0 * kC0 * kC0);   // [F/m]
+
+constexpr int kMaxSrc = 8;    // sources fused into one step launch
+constexpr int kMaxPrb = 32;   // probes fused into one step launch
+
+// Device error word bits.
+enum : int { kErrIndex = 1, kErrTimeout = 2 };
+
+struct EdgeRef {
+    int axis, i, j, k;
+};
+
+// One leapfrog member: a state pair plus its place in absolute time.
+struct Member {
+    void *st[2];            // two 6*ncell state blocks (T)
+    long long start;        // absolute step of the member at iteration 0
+    long long src_lo;       // sources act for absolute steps in [src_lo, src_hi)
+    long long src_hi;
+    double *probe;          // probe rows, row = absolute step - probe_base
+    long long probe_base;
+    double *energy;         // energy[absolute step - energy_base]
+    long long energy_base;
+};
+
+// Arguments of one fused leapfrog launch (all members advance one step).
+template <typename T>
+struct StepArgs {
+    int nx, ny, nz;
+    long long ncell;
+    int tiles_x, tiles_y, nchunk, kz;
+    const T *ca;    // 3*ncell, or null when the grid is lossless (ca = 1)
+    const T *cb;    // 3*ncell
+    const T *ch;    // 3 values (uniform mu) or 3*ncell (per face)
+    const T *meps;  // 3*ncell, energy only
+    const T *mmu;   // 3 values or 3*ncell, energy only
+    const Member *mem;
+    int nmem;       // members in this launch (table prefix)
+    int it;         // iteration: member m is at absolute step mem[m].start + it
+    int parity;     // read st[parity], write st[parity ^ 1]
+    const double *amp;      // source amplitudes amp[(step - amp_base)*nsrc + s]
+    long long amp_base;
+    long long amp_len;
+    int nsrc;
+    EdgeRef src[kMaxSrc];
+    int nprb;
+    EdgeRef prb[kMaxPrb];
+    int *err;
+};
+
+struct Tile {
+    int tx, ty, kz;
+};
+
+// step.cu
+template <typename T>
+cudaError_t launch_step(const StepArgs<T> &a, Tile tile, bool lossy, bool mu_array, bool energy,
+                        cudaStream_t s);
+bool tile_supported(int tx, int ty);
+
+// aux.cu
+struct MaterialFlags {
+    int bad_eps, bad_mu, bad_sigma, mu_nonuniform, lossy;
+    float eps_mu_min;
+};
+cudaError_t check_materials(const float *eps, const float *mu, const float *sig, long long ncell,
+                            MaterialFlags *flags_host, void *scratch, cudaStream_t s);
+template <typename T>
+cudaError_t build_coeffs(int nx, int ny, int nz, const double d[3], const float *eps, const float *mu,
+                         const float *sig, double dt, int scheme, bool mu_array, T *ca, T *cb, T *ch,
+                         T *meps, T *mmu, cudaStream_t s);
+cudaError_t source_table(const fit_source *src_dev, int nsrc, long long base, long long len, double dt,
+                         double *amp, cudaStream_t s);
+template <typename T>
+cudaError_t mask_state(int nx, int ny, int nz, T *e, T *h, cudaStream_t s);
+template <typename T>
+cudaError_t accumulate_state(long long n6, const T *st, double *acc, cudaStream_t s);
+template <typename T>
+cudaError_t accumulate_state_kahan(long long n6, const T *st, float *sum, float *comp, cudaStream_t s);
+cudaError_t kahan_finish(long long n, const float *sum, const float *comp, double *out, cudaStream_t s);
+cudaError_t sum_members(int nmem, long long len, const double *per_member, long long stride, double *out,
+                        cudaStream_t s);
+template <typename Tin, typename Tout>
+cudaError_t convert_copy(long long n, const Tin *in, Tout *out, cudaStream_t s);
+
+}  // namespace fitgb
