@@ -34,7 +34,7 @@ class _Grid(ctypes.Structure):
         ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
         ("d", ctypes.c_double * 3), ("dt", ctypes.c_double),
         ("ca", ctypes.c_void_p), ("cb", ctypes.c_void_p), ("ch", ctypes.c_void_p),
-        ("meps", ctypes.c_void_p), ("mmu", ctypes.c_void_p),
+        ("meps", ctypes.c_void_p), ("mmu", ctypes.c_void_p), ("store32", ctypes.c_int),
     ]
 
 
@@ -133,10 +133,13 @@ class OracleGrid:
     """A grid with its FP64 material matrices and leapfrog coefficients.
 
     ``round32`` rounds ca, cb, ch to float, as stored by an FP32 field path.
+    ``store32`` also rounds every stored e and h value to float after its
+    update (arithmetic stays FP64): the error model of keeping the fields in
+    float, used only to derive FP32 test tolerances.
     """
 
     def __init__(self, dims, spacing, eps_r, mu_r=None, sigma=None, dt=None,
-                 cfl_fraction=0.95, sigma_scheme=0, round32=False):
+                 cfl_fraction=0.95, sigma_scheme=0, round32=False, store32=False):
         self.nx, self.ny, self.nz = (int(v) for v in dims)
         self.spacing = tuple(float(v) for v in spacing)
         shp = (self.nz, self.ny, self.nx)
@@ -161,7 +164,7 @@ class OracleGrid:
             raise ValueError(f"oracle_coeffs failed ({rc})")
         self._g = _Grid(self.nx, self.ny, self.nz, (ctypes.c_double * 3)(*self.spacing), self.dt,
                         _ptr(self.ca).value, _ptr(self.cb).value, _ptr(self.ch).value,
-                        _ptr(self.meps).value, _ptr(self.mmu).value)
+                        _ptr(self.meps).value, _ptr(self.mmu).value, int(bool(store32)))
 
     def zeros(self):
         return np.zeros(self.field_shape)

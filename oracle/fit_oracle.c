@@ -46,6 +46,10 @@ typedef struct {
     const double *ch;     /* 3*Np: h <- h - ch*(C e)                          */
     const double *meps;   /* 3*Np: diagonal of M_eps (for the energy)         */
     const double *mmu;    /* 3*Np: diagonal of M_mu                           */
+    int store32;          /* 1: round every stored e, h to float after its    */
+                          /* update (exact arithmetic, FP32 storage): the     */
+                          /* error model of a method that keeps its fields in */
+                          /* float, used to derive FP32 tolerances            */
 } or_grid;
 
 typedef struct { int axis, i, j, k, waveform; double amp, f0, width, delay; } or_source;
@@ -299,6 +303,7 @@ int oracle_leapfrog(const or_grid *g, long nsteps, long step0, long src_lo, long
                         long p = (long)a * Np + pidx(nx, ny, i, j, k);
                         double hold = h[p];
                         double hnew = hold - g->ch[p] * curl_e(e, nx, ny, Np, a, q);
+                        if (g->store32) hnew = (double)(float)hnew;
                         w_h += g->mmu[p] * hold * hnew;
                         h[p] = hnew;
                     }
@@ -318,6 +323,7 @@ int oracle_leapfrog(const or_grid *g, long nsteps, long step0, long src_lo, long
                                                             src[s].width, src[s].delay,
                                                             ((double)abs_step + 0.5) * g->dt);
                         e[p] = g->ca[p] * e[p] + g->cb[p] * (curl_h(h, nx, ny, Np, a, q) - jsrc);
+                        if (g->store32) e[p] = (double)(float)e[p];
                     }
         if (probe_out)
             for (int p = 0; p < nprb; ++p)

@@ -40,7 +40,7 @@ struct fit_grid {
     long long ncell = 0;
     float *eps = nullptr, *mu = nullptr, *sig = nullptr;
     bool mu_array = false, lossy = false;
-    float eps_mu_min = 1.f;
+    double eps_mu_min = 1.0;
     // coefficient cache
     bool c_valid = false, c_has_energy = false;
     double c_dt = 0.0;

@@ -2,6 +2,7 @@
 // leapfrog coefficients, source tables, state masking and the ParaExp
 // superposition sums.
 #include <cmath>
+#include <cstring>
 
 #include "internal.h"
 
@@ -16,10 +17,11 @@ inline unsigned grid_for(long long n, int per = kThreads) {
     return (unsigned)(b > 0 ? b : 1);
 }
 
-// flags[0..4]: bad_eps, bad_mu, bad_sigma, mu_nonuniform, lossy; flags[5]: min(eps*mu) bits
-__global__ void check_kernel(const float *eps, const float *mu, const float *sig, long long n, int *flags) {
+// flags[0..4]: bad_eps, bad_mu, bad_sigma, mu_nonuniform, lossy; *mnbits: min(eps*mu) as FP64 bits
+__global__ void check_kernel(const float *eps, const float *mu, const float *sig, long long n, int *flags,
+                             unsigned long long *mnbits) {
     int bad_e = 0, bad_m = 0, bad_s = 0, nonu = 0, lossy = 0;
-    float mn = INFINITY;
+    double mn = INFINITY;
     const float mu_ref = mu ? mu[0] : 1.0f;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const float e = eps[c];
@@ -30,7 +32,7 @@ __global__ void check_kernel(const float *eps, const float *mu, const float *sig
         if (!(s >= 0.0f) || !isfinite(s)) bad_s = 1;
         if (m != mu_ref) nonu = 1;
         if (s != 0.0f) lossy = 1;
-        const float em = e * m;
+        const double em = (double)e * (double)m;
         if (em < mn) mn = em;
     }
     bad_e = __syncthreads_or(bad_e);
@@ -38,7 +40,7 @@ __global__ void check_kernel(const float *eps, const float *mu, const float *sig
     bad_s = __syncthreads_or(bad_s);
     nonu = __syncthreads_or(nonu);
     lossy = __syncthreads_or(lossy);
-    for (int off = 16; off > 0; off >>= 1) mn = fminf(mn, __shfl_down_sync(0xffffffffu, mn, off));
+    for (int off = 16; off > 0; off >>= 1) mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, off));
     if (threadIdx.x == 0) {
         if (bad_e) atomicOr(flags + 0, 1);
         if (bad_m) atomicOr(flags + 1, 1);
@@ -46,7 +48,9 @@ __global__ void check_kernel(const float *eps, const float *mu, const float *sig
         if (nonu) atomicOr(flags + 3, 1);
         if (lossy) atomicOr(flags + 4, 1);
     }
-    if ((threadIdx.x & 31) == 0 && mn >= 0.0f && isfinite(mn)) atomicMin(flags + 5, __float_as_int(mn));
+    // non-negative doubles order like their bit patterns
+    if ((threadIdx.x & 31) == 0 && mn >= 0.0 && isfinite(mn))
+        atomicMin(mnbits, (unsigned long long)__double_as_longlong(mn));
 }
 
 // Leapfrog coefficients of one point (i,j,k): its three edges and three faces.
@@ -227,12 +231,15 @@ __global__ void convert_kernel(long long n, const Tin *in, Tout *out) {
 cudaError_t check_materials(const float *eps, const float *mu, const float *sig, long long ncell,
                             MaterialFlags *out, void *scratch, cudaStream_t s) {
     int *flags = static_cast<int *>(scratch);
-    int init[6] = {0, 0, 0, 0, 0, 0x7f800000};   // +inf bits for the min
+    unsigned long long *mnbits = reinterpret_cast<unsigned long long *>(flags + 8);
+    int init[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const double inf = INFINITY;
+    memcpy(&init[8], &inf, sizeof(double));
     cudaError_t err = cudaMemcpyAsync(flags, init, sizeof(init), cudaMemcpyHostToDevice, s);
     if (err != cudaSuccess) return err;
-    check_kernel<<<grid_for(ncell), kThreads, 0, s>>>(eps, mu, sig, ncell, flags);
+    check_kernel<<<grid_for(ncell), kThreads, 0, s>>>(eps, mu, sig, ncell, flags, mnbits);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    int h[6];
+    int h[10];
     if ((err = cudaMemcpyAsync(h, flags, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return err;
     if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return err;
     out->bad_eps = h[0];
@@ -240,8 +247,8 @@ cudaError_t check_materials(const float *eps, const float *mu, const float *sig,
     out->bad_sigma = h[2];
     out->mu_nonuniform = h[3];
     out->lossy = h[4];
-    float mn;
-    memcpy(&mn, &h[5], sizeof(float));
+    double mn;
+    memcpy(&mn, &h[8], sizeof(double));
     out->eps_mu_min = mn;
     return cudaSuccess;
 }

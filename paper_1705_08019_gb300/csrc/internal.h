@@ -80,7 +80,7 @@ bool tile_supported(int tx, int ty);
 // aux.cu
 struct MaterialFlags {
     int bad_eps, bad_mu, bad_sigma, mu_nonuniform, lossy;
-    float eps_mu_min;
+    double eps_mu_min;
 };
 cudaError_t check_materials(const float *eps, const float *mu, const float *sig, long long ncell,
                             MaterialFlags *flags_host, void *scratch, cudaStream_t s);

@@ -205,7 +205,7 @@ def small_random(dims=(12, 10, 8), spacing=(1e-3, 1.2e-3, 0.9e-3), seed: int = S
     mu_r = rng.uniform(1.0, 3.0, size=(nz, ny, nx)).astype(np.float32) if mu else None
     dmin = min(spacing)
     srcs = [band_source(2, nx // 2, ny // 2, nz // 2, dmin, 6.0),
-            dict(band_source(0, nx // 3, ny // 3, nz // 3, dmin, 6.0), amp=0.5)]
+            dict(band_source(0, nx // 3, max(1, ny // 3), max(1, nz // 3), dmin, 6.0), amp=0.5)]
     prbs = [dict(axis=2, i=1, j=2, k=1), dict(axis=0, i=nx - 2, j=ny - 2, k=nz // 2),
             dict(axis=1, i=nx // 2, j=1, k=nz - 2), dict(axis=2, i=nx - 3, j=ny // 2, k=nz - 1)]
     return Workload(name=f"small{nx}x{ny}x{nz}", dims=dims, spacing=spacing, eps_r=eps, mu_r=mu_r,
