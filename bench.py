@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--compare-plain", action="store_true",
                     help="also time the K windows run one after another (members_per_pass=1)")
+    ap.add_argument("--ncu-case", choices=["leapfrog", "paraexp"], default=None,
+                    help="run a short untimed case for an ncu capture and exit (no JSON line)")
+    ap.add_argument("--ncu-steps", type=int, default=8)
+    ap.add_argument("--ncu-members", type=int, default=4)
     return ap.parse_args()
 
 
@@ -336,8 +340,37 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
+def ncu_case(args):
+    """A short run of the step kernel on the full-size grid for ncu: either a
+    single-member leapfrog of --ncu-steps steps, or a ParaExp with
+    --ncu-members windows of one step each plus the rest of --ncu-steps
+    (every launch advances all still-active members)."""
+    import torch
+    from paper_1705_08019_gb300 import build as B
+    from paper_1705_08019_gb300 import fitgb
+    B.build()
+    w = load_workload(args.workload)
+    dev = torch.device("cuda", 0)
+    eps = torch.from_numpy(w.eps_r).to(dev)
+    sig = torch.from_numpy(w.sigma).to(dev) if w.sigma is not None else None
+    g = fitgb.fit_grid_create(w.dims, w.spacing, eps, None, sig, w.precision)
+    dt = w.cfl_fraction * fitgb.fit_cfl_dt(g)
+    s = torch.cuda.current_stream(dev)
+    if args.ncu_case == "leapfrog":
+        fitgb.fit_leapfrog_run(g, dt, args.ncu_steps, 0, w.sources, w.probes, None, None, None, None, None, s)
+    else:
+        K = args.ncu_members
+        win = np.array([j for j in range(K)] + [args.ncu_steps], dtype=np.int64)
+        fitgb.paraexp_run(g, dt, K, win, w.sources, w.probes, None, None, None, None, None, None, s)
+    torch.cuda.synchronize()
+    fitgb.fit_grid_destroy(g)
+
+
 def main():
     args = parse()
+    if args.ncu_case:
+        ncu_case(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
