@@ -66,7 +66,7 @@ def load_workload(name):
 
 def config_of(w, extra=None):
     nx, ny, nz = w.dims
-    state_bytes = 2 * 6 * (4 if w.precision == 32 else 8) * w.ncell * w.K
+    state_bytes = 2 * 6 * (4 if w.precision == 32 else 8) * w.ncells * w.K
     cfg = {"workload": w.name, "cells": f"{nx}x{ny}x{nz}", "nsteps": w.nsteps, "K": w.K,
            "precision": f"fp{w.precision}", "lossy": w.sigma is not None,
            "l2": ("inputs larger than L2: %.1f GB of member state" % (state_bytes / 1e9))
@@ -80,7 +80,7 @@ def config_of(w, extra=None):
 def work_of(w):
     """cell-updates of one ParaExp solve with equal windows (Sec. III)."""
     win = w.windows()
-    return int(sum(int(win[-1] - win[j]) for j in range(w.K))) * w.ncell
+    return int(sum(int(win[-1] - win[j]) for j in range(w.K))) * w.ncells
 
 
 # ---------------------------------------------------------------------------
@@ -99,7 +99,7 @@ def oracle_sample(w, nsteps=4, K=2):
     win = np.array([(j * nsteps) // K for j in range(K + 1)], dtype=np.int64)
     g.paraexp(K, win, w.sources, w.probes)
     sec = time.perf_counter() - t0
-    work = int(sum(int(win[-1] - win[j]) for j in range(K))) * w.ncell
+    work = int(sum(int(win[-1] - win[j]) for j in range(K))) * w.ncells
     desc = (f"oracle (serial FP64 C) on the full {w.dims[0]}x{w.dims[1]}x{w.dims[2]} grid: coefficient build + "
             f"ParaExp of {nsteps} steps in {K} windows ({work:.3g} cell-updates)")
     return work / sec / 1e9, sec, desc
