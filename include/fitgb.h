@@ -99,6 +99,8 @@ typedef struct {
     int force_dt;               /* 1: accept dt above the CFL estimate [0]    */
     int profile;                /* 1: time every step launch with CUDA events
                                    on the run's stream (fit_last_stats) [0]   */
+    int kernel;                 /* step kernel: 1 shared-memory staging by
+                                   plain loads, 2 TMA pipeline [0 = 2]        */
 } fit_run_opts;
 
 /* Counters of the last leapfrog / ParaExp run on a grid.  step_ms is the

@@ -37,7 +37,9 @@ struct fit_grid {
     int nx = 0, ny = 0, nz = 0;
     double d[3] = {0, 0, 0};
     int prec = 32;
-    long long ncell = 0;
+    long long ncell = 0;   // nx*ny*nz
+    int pitch = 0;         // padded row length (multiple of 4)
+    long long ncp = 0;     // pitch*ny*nz: padded component stride
     float *eps = nullptr, *mu = nullptr, *sig = nullptr;
     bool mu_array = false, lossy = false;
     double eps_mu_min = 1.0;
@@ -45,11 +47,11 @@ struct fit_grid {
     bool c_valid = false, c_has_energy = false;
     double c_dt = 0.0;
     int c_scheme = -1;
-    Buf ca, cb, ch, meps, mmu;
+    Buf coef, ch, meps, mmu;   // coef: cb (3 components) then ca (3, lossy only)
     // workspaces
     Buf state, pm, amp, srcdev, memdev, acc, kahan, stage, energy, scratch, probe_ws, err;
     int deferred = 0;
-    Tile tile = {32, 8, 32};
+    Tile tile = {32, 8, 32, 2};
     bool tile_fixed = false;
     fit_run_stats stats = {0, 0, 0, 0.0, 0.0};
     std::vector<cudaEvent_t> ev;   // pool for per-launch timing (opts->profile)
@@ -133,20 +135,21 @@ bool edge_is_dof(const fit_grid *g, int axis, int i, int j, int k) {
 template <typename T>
 int ensure_coeffs(fit_grid *g, double dt, int scheme, bool need_energy, cudaStream_t s) {
     if (g->c_valid && g->c_dt == dt && g->c_scheme == scheme && (!need_energy || g->c_has_energy)) return FIT_OK;
-    const size_t n3 = 3 * (size_t)g->ncell * sizeof(T);
+    const size_t n3 = 3 * (size_t)g->ncp * sizeof(T);
     const size_t nch = g->mu_array ? n3 : 3 * sizeof(T);
     int rc;
-    if (g->lossy && (rc = ensure(g->ca, n3))) return rc;
-    if ((rc = ensure(g->cb, n3))) return rc;
+    if ((rc = ensure(g->coef, g->lossy ? 2 * n3 : n3))) return rc;
     if ((rc = ensure(g->ch, nch))) return rc;
     const bool energy = need_energy || g->c_has_energy;
     if (energy) {
         if ((rc = ensure(g->meps, n3))) return rc;
         if ((rc = ensure(g->mmu, nch))) return rc;
     }
-    FIT_CHECK(build_coeffs<T>(g->nx, g->ny, g->nz, g->d, g->eps, g->mu, g->sig, dt, scheme, g->mu_array,
-                              g->lossy ? (T *)g->ca.p : nullptr, (T *)g->cb.p, (T *)g->ch.p,
-                              energy ? (T *)g->meps.p : nullptr, energy ? (T *)g->mmu.p : nullptr, s));
+    T *cb = (T *)g->coef.p;
+    T *ca = g->lossy ? cb + 3 * g->ncp : nullptr;
+    FIT_CHECK(build_coeffs<T>(g->nx, g->ny, g->nz, g->pitch, g->d, g->eps, g->mu, g->sig, dt, scheme, g->mu_array,
+                              ca, cb, (T *)g->ch.p, energy ? (T *)g->meps.p : nullptr,
+                              energy ? (T *)g->mmu.p : nullptr, s));
     g->stats.kernel_launches += 1;
     g->c_valid = true;
     g->c_dt = dt;
@@ -162,9 +165,15 @@ struct MemberSpec {
 
 Tile pick_tile(const fit_grid *g, const fit_run_opts *o) {
     Tile t = g->tile;
-    if (o && o->tile_x > 0 && o->tile_y > 0 && tile_supported(o->tile_x, o->tile_y)) {
+    if (o && o->kernel > 0) t.kernel = o->kernel;
+    if (o && o->tile_x > 0 && o->tile_y > 0) {
         t.tx = o->tile_x;
         t.ty = o->tile_y;
+    }
+    if (t.kernel == 2 && !tma_tile_supported(t.tx, t.ty)) t.kernel = 1;
+    if (t.kernel == 1 && !tile_supported(t.tx, t.ty)) {
+        t.tx = 32;
+        t.ty = 8;
     }
     if (o && o->tile_z > 0) t.kz = o->tile_z;
     if (t.kz <= 0) t.kz = 32;
@@ -177,16 +186,19 @@ Tile pick_tile(const fit_grid *g, const fit_run_opts *o) {
 // Run `specs` members, iteration-aligned; see the file comment.
 //   probe_dev: (probe rows) x nprb device buffer to receive the probe sum, or null
 //   energy_dev: device buffer (rows) for member 0's energy, or null
-//   acc: superposition target (FP64, 6*ncell: e then h), or null
-//   final_state: copy member 0's final state here (T*, 6*ncell layout: e|h) or null
+//   acc_e, acc_h: padded FP64 superposition targets (3 components each), or null
+//   final_e, final_h: copy member 0's final state here (compact layout), or null
 template <typename T>
 int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec> &specs_in,
                 long long amp_base, long long amp_len, const fit_source *src, int nsrc, const fit_probe *prb,
                 int nprb, long long probe_base, long long probe_rows, double *probe_dev, double *energy_dev,
                 int sum_mode, double *acc_e, double *acc_h, void *final_e, void *final_h,
                 const fit_run_opts *opts, cudaStream_t s) {
-    const long long ncell = g->ncell;
-    const size_t n6 = 6 * (size_t)ncell;
+    const long long ncell = g->ncell;   // real cells (algorithmic counts)
+    const long long ncp = g->ncp;       // padded component stride (device arrays)
+    const size_t n6 = 6 * (size_t)ncp;
+    const size_t row = (size_t)g->nx * sizeof(T), prow = (size_t)g->pitch * sizeof(T);
+    const size_t rows3 = 3 * (size_t)g->ny * g->nz;
     int rc;
     if (nsrc > kMaxSrc || nprb > kMaxPrb) return FIT_ERR_UNSUPPORTED;
     g->stats = fit_run_stats{0, 0, 0, 0.0, 0.0};
@@ -228,19 +240,19 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
         if ((rc = ensure(g->kahan, 2 * n6 * sizeof(float)))) return rc;
         FIT_CHECK(cudaMemsetAsync(g->kahan.p, 0, 2 * n6 * sizeof(float), s));
     }
-    if (acc_e) FIT_CHECK(cudaMemsetAsync(acc_e, 0, 3 * ncell * sizeof(double), s));
-    if (acc_h) FIT_CHECK(cudaMemsetAsync(acc_h, 0, 3 * ncell * sizeof(double), s));
+    if (acc_e) FIT_CHECK(cudaMemsetAsync(acc_e, 0, 3 * ncp * sizeof(double), s));
+    if (acc_h) FIT_CHECK(cudaMemsetAsync(acc_h, 0, 3 * ncp * sizeof(double), s));
 
     StepArgs<T> a;
     memset(&a, 0, sizeof(a));
-    const Tile tile = pick_tile(g, opts);
-    a.nx = g->nx; a.ny = g->ny; a.nz = g->nz; a.ncell = ncell;
+    Tile tile = pick_tile(g, opts);
+    a.nx = g->nx; a.ny = g->ny; a.nz = g->nz; a.pitch = g->pitch; a.ncell = ncp;
     a.tiles_x = (g->nx + tile.tx - 1) / tile.tx;
     a.tiles_y = (g->ny + tile.ty - 1) / tile.ty;
     a.kz = tile.kz;
     a.nchunk = (g->nz + tile.kz - 1) / tile.kz;
-    a.ca = g->lossy ? (const T *)g->ca.p : nullptr;
-    a.cb = (const T *)g->cb.p;
+    a.cb = (const T *)g->coef.p;
+    a.ca = g->lossy ? (const T *)g->coef.p + 3 * ncp : nullptr;
     a.ch = (const T *)g->ch.p;
     a.meps = energy_dev ? (const T *)g->meps.p : nullptr;
     a.mmu = energy_dev ? (const T *)g->mmu.p : nullptr;
@@ -253,6 +265,13 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
     a.nprb = probes ? nprb : 0;
     for (int q = 0; q < nprb; ++q) a.prb[q] = {prb[q].axis, prb[q].i, prb[q].j, prb[q].k};
     a.err = (int *)g->err.p;
+    TmaMaps maps;
+    if (tile.kernel == 2 &&
+        !encode_tma_maps(&maps, (int)sizeof(T), g->nx, g->ny, g->nz, g->pitch, g->state.p, 2 * mpp, g->coef.p,
+                         g->lossy ? 6 : 3, tile.tx, tile.ty)) {
+        tile.kernel = 1;
+        if (!tile_supported(tile.tx, tile.ty)) tile.tx = 32, tile.ty = 8;
+    }
 
     // Groups run from the end of the table (shortest members) to its start, and
     // inside a group members finish shortest first, so the superposition adds
@@ -266,6 +285,8 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
             T *base = (T *)g->state.p + 2 * n6 * (size_t)q;
             mem[q].st[0] = base;
             mem[q].st[1] = base + n6;
+            mem[q].blk[0] = 2 * q;
+            mem[q].blk[1] = 2 * q + 1;
             mem[q].start = sp.start;
             mem[q].src_lo = sp.src_lo;
             mem[q].src_hi = sp.src_hi;
@@ -275,11 +296,12 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
             mem[q].energy_base = sp.start;
             // initial state into buffer 0
             FIT_CHECK(cudaMemsetAsync(base, 0, n6 * sizeof(T), s));
-            if (sp.e0) FIT_CHECK(cudaMemcpyAsync(base, sp.e0, 3 * ncell * sizeof(T), kind_to_dev(sp.e0), s));
+            if (sp.e0)
+                FIT_CHECK(cudaMemcpy2DAsync(base, prow, sp.e0, row, row, rows3, kind_to_dev(sp.e0), s));
             if (sp.h0)
-                FIT_CHECK(cudaMemcpyAsync(base + 3 * ncell, sp.h0, 3 * ncell * sizeof(T), kind_to_dev(sp.h0), s));
+                FIT_CHECK(cudaMemcpy2DAsync(base + 3 * ncp, prow, sp.h0, row, row, rows3, kind_to_dev(sp.h0), s));
             if (sp.e0 || sp.h0) {
-                FIT_CHECK(mask_state<T>(g->nx, g->ny, g->nz, base, base + 3 * ncell, s));
+                FIT_CHECK(mask_state<T>(g->nx, g->ny, g->nz, g->pitch, base, base + 3 * ncp, s));
                 g->stats.kernel_launches += 1;
             }
         }
@@ -302,7 +324,10 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
                 }
                 FIT_CHECK(cudaEventRecord(g->ev[2 * nev], s));
             }
-            FIT_CHECK(launch_step<T>(a, tile, g->lossy, g->mu_array, energy_dev != nullptr, s));
+            if (tile.kernel == 2)
+                FIT_CHECK(launch_step_tma<T>(a, maps, tile, g->lossy, g->mu_array, energy_dev != nullptr, s));
+            else
+                FIT_CHECK(launch_step<T>(a, tile, g->lossy, g->mu_array, energy_dev != nullptr, s));
             if (profile) {
                 FIT_CHECK(cudaEventRecord(g->ev[2 * nev + 1], s));
                 ++nev;
@@ -322,20 +347,20 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
                         FIT_CHECK(accumulate_state_kahan<T>((long long)n6, fin, ks, ks + n6, s));
                         g->stats.kernel_launches += 1;
                     } else {
-                        FIT_CHECK(accumulate_state<T>(3 * ncell, fin, acc_e, s));
+                        FIT_CHECK(accumulate_state<T>(3 * ncp, fin, acc_e, s));
                         g->stats.kernel_launches += 1;
                         if (acc_h) {
-                            FIT_CHECK(accumulate_state<T>(3 * ncell, fin + 3 * ncell, acc_h, s));
+                            FIT_CHECK(accumulate_state<T>(3 * ncp, fin + 3 * ncp, acc_h, s));
                             g->stats.kernel_launches += 1;
                         }
                     }
                 }
                 if (order[first + q] == 0) {
                     if (final_e)
-                        FIT_CHECK(cudaMemcpyAsync(final_e, fin, 3 * ncell * sizeof(T), kind_from_dev(final_e), s));
+                        FIT_CHECK(cudaMemcpy2DAsync(final_e, row, fin, prow, row, rows3, kind_from_dev(final_e), s));
                     if (final_h)
-                        FIT_CHECK(cudaMemcpyAsync(final_h, fin + 3 * ncell, 3 * ncell * sizeof(T),
-                                                  kind_from_dev(final_h), s));
+                        FIT_CHECK(cudaMemcpy2DAsync(final_h, row, fin + 3 * ncp, prow, row, rows3,
+                                                    kind_from_dev(final_h), s));
                 }
             }
         }
@@ -345,23 +370,25 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
             if (sp.nit > 0) continue;
             const T *fin = (const T *)mem[q].st[0];
             if (acc_e && !kahan) {
-                FIT_CHECK(accumulate_state<T>(3 * ncell, fin, acc_e, s));
-                if (acc_h) FIT_CHECK(accumulate_state<T>(3 * ncell, fin + 3 * ncell, acc_h, s));
+                FIT_CHECK(accumulate_state<T>(3 * ncp, fin, acc_e, s));
+                if (acc_h) FIT_CHECK(accumulate_state<T>(3 * ncp, fin + 3 * ncp, acc_h, s));
             } else if (kahan) {
                 float *ks = (float *)g->kahan.p;
                 FIT_CHECK(accumulate_state_kahan<T>((long long)n6, fin, ks, ks + n6, s));
             }
             if (order[first + q] == 0) {
-                if (final_e) FIT_CHECK(cudaMemcpyAsync(final_e, fin, 3 * ncell * sizeof(T), kind_from_dev(final_e), s));
+                if (final_e)
+                    FIT_CHECK(cudaMemcpy2DAsync(final_e, row, fin, prow, row, rows3, kind_from_dev(final_e), s));
                 if (final_h)
-                    FIT_CHECK(cudaMemcpyAsync(final_h, fin + 3 * ncell, 3 * ncell * sizeof(T), kind_from_dev(final_h), s));
+                    FIT_CHECK(cudaMemcpy2DAsync(final_h, row, fin + 3 * ncp, prow, row, rows3,
+                                                kind_from_dev(final_h), s));
             }
         }
     }
     if (kahan) {
         float *ks = (float *)g->kahan.p;
-        FIT_CHECK(kahan_finish(3 * ncell, ks, ks + n6, acc_e, s));
-        if (acc_h) FIT_CHECK(kahan_finish(3 * ncell, ks + 3 * ncell, ks + n6 + 3 * ncell, acc_h, s));
+        FIT_CHECK(kahan_finish(3 * ncp, ks, ks + n6, acc_e, s));
+        if (acc_h) FIT_CHECK(kahan_finish(3 * ncp, ks + 3 * ncp, ks + n6 + 3 * ncp, acc_h, s));
     }
     if (kahan) g->stats.kernel_launches += acc_h ? 2 : 1;
     if (probes) {
@@ -476,17 +503,11 @@ int paraexp_impl(fit_grid *g, double dt, int K, const long *win, const fit_sourc
         }
     }
     double *ae = nullptr, *ah = nullptr;
-    const size_t n3 = 3 * (size_t)g->ncell;
+    const size_t n3 = 3 * (size_t)g->ncp;
     if (e_final || h_final) {
-        const bool both_dev = e_final && h_final && is_device(e_final) && is_device(h_final);
-        if (both_dev) {
-            ae = e_final;
-            ah = h_final;
-        } else {
-            if ((rc = ensure(g->acc, 2 * n3 * sizeof(double)))) return rc;
-            ae = (double *)g->acc.p;
-            ah = ae + n3;
-        }
+        if ((rc = ensure(g->acc, 2 * n3 * sizeof(double)))) return rc;
+        ae = (double *)g->acc.p;
+        ah = ae + n3;
     }
     const int sum_mode = opts ? opts->sum_mode : 0;
     rc = run_members<T>(g, dt, scheme, specs, W0, nt, src, nsrc, prb, nprb, W0, nt, pdev, nullptr, sum_mode, ae, ah,
@@ -494,10 +515,10 @@ int paraexp_impl(fit_grid *g, double dt, int K, const long *win, const fit_sourc
     if (rc) return rc;
     if (pdev && pdev != probe_out)
         FIT_CHECK(cudaMemcpyAsync(probe_out, pdev, sizeof(double) * (size_t)nt * nprb, cudaMemcpyDeviceToHost, s));
-    if (ae && ae != e_final) {
-        if (e_final) FIT_CHECK(cudaMemcpyAsync(e_final, ae, n3 * sizeof(double), kind_from_dev(e_final), s));
-        if (h_final) FIT_CHECK(cudaMemcpyAsync(h_final, ah, n3 * sizeof(double), kind_from_dev(h_final), s));
-    }
+    const size_t row = (size_t)g->nx * sizeof(double), prow = (size_t)g->pitch * sizeof(double);
+    const size_t rows3 = 3 * (size_t)g->ny * g->nz;
+    if (e_final) FIT_CHECK(cudaMemcpy2DAsync(e_final, row, ae, prow, row, rows3, kind_from_dev(e_final), s));
+    if (h_final) FIT_CHECK(cudaMemcpy2DAsync(h_final, row, ah, prow, row, rows3, kind_from_dev(h_final), s));
     return finish(g, s, host_out);
 }
 
@@ -538,6 +559,8 @@ int fit_grid_create(int nx, int ny, int nz, double dx, double dy, double dz, con
     g->d[0] = dx; g->d[1] = dy; g->d[2] = dz;
     g->prec = precision;
     g->ncell = ncell;
+    g->pitch = pitch_of(nx);
+    g->ncp = (long long)g->pitch * ny * nz;
     const size_t bytes = sizeof(float) * (size_t)ncell;
     cudaStream_t s = 0;
     auto fail = [&](int rc) {
@@ -571,7 +594,7 @@ void fit_grid_destroy(fit_grid *g) {
     if (g->eps) cudaFree(g->eps);
     if (g->mu) cudaFree(g->mu);
     if (g->sig) cudaFree(g->sig);
-    Buf *bufs[] = {&g->ca, &g->cb, &g->ch, &g->meps, &g->mmu, &g->state, &g->pm, &g->amp, &g->srcdev,
+    Buf *bufs[] = {&g->coef, &g->ch, &g->meps, &g->mmu, &g->state, &g->pm, &g->amp, &g->srcdev,
                    &g->memdev, &g->acc, &g->kahan, &g->stage, &g->energy, &g->scratch, &g->probe_ws, &g->err};
     for (Buf *b : bufs) release(*b);
     for (cudaEvent_t e : g->ev) cudaEventDestroy(e);

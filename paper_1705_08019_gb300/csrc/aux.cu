@@ -59,25 +59,26 @@ __global__ void check_kernel(const float *eps, const float *mu, const float *sig
 // are the correctly rounded results of the stated operations in the stated
 // order.
 template <typename T>
-__global__ void coeff_kernel(int nx, int ny, int nz, double d0, double d1, double d2, const float *eps,
+__global__ void coeff_kernel(int nx, int ny, int nz, int pitch, double d0, double d1, double d2, const float *eps,
                              const float *mu, const float *sig, double dt, int scheme, int mu_array,
                              T *ca, T *cb, T *ch, T *meps, T *mmu) {
-    const long long ncell = (long long)nx * ny * nz;
-    const int n[3] = {nx, ny, nz};
+    const long long ncell = (long long)pitch * ny * nz;   // padded component stride
     const double d[3] = {d0, d1, d2};
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
          c += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(c % nx);
-        const int j = (int)((c / nx) % ny);
-        const int k = (int)(c / ((long long)nx * ny));
+        const int i = (int)(c % pitch);
+        const int j = (int)((c / pitch) % ny);
+        const int k = (int)(c / ((long long)pitch * ny));
         const int q[3] = {i, j, k};
+        const long long cell = (long long)i + (long long)nx * ((long long)j + (long long)ny * k);
+        const bool pad = i >= nx;
         for (int a = 0; a < 3; ++a) {
             const int b = (a + 1) % 3, cc = (a + 2) % 3;
             const double len = d[a];
             const double area = __dmul_rn(d[b], d[cc]);
             const long long o = (long long)a * ncell + c;
             // edge along a: a degree of freedom iff both other indices are > 0
-            if (q[b] > 0 && q[cc] > 0) {
+            if (!pad && q[b] > 0 && q[cc] > 0) {
                 double esum = 0.0, ssum = 0.0;
                 for (int sb = 0; sb < 2; ++sb)
                     for (int sc = 0; sc < 2; ++sc) {
@@ -111,11 +112,11 @@ __global__ void coeff_kernel(int nx, int ny, int nz, double d0, double d1, doubl
             // face normal to a: interior iff q[a] > 0
             if (mu_array) {
                 T vch = T(0), vmm = T(0);
-                if (q[a] > 0) {
+                if (!pad && q[a] > 0) {
                     int r[3] = {q[0], q[1], q[2]};
                     r[a] -= 1;
                     const long long rc = (long long)r[0] + (long long)nx * ((long long)r[1] + (long long)ny * r[2]);
-                    const double m1 = mu ? (double)mu[c] : 1.0;
+                    const double m1 = mu ? (double)mu[cell] : 1.0;
                     const double m2 = mu ? (double)mu[rc] : 1.0;
                     const double mt = __ddiv_rn(2.0, __dadd_rn(__ddiv_rn(1.0, m1), __ddiv_rn(1.0, m2)));
                     const double Mm = __ddiv_rn(__dmul_rn(__dmul_rn(kMu0, mt), area), len);
@@ -163,24 +164,25 @@ __global__ void source_kernel(const fit_source *src, int nsrc, long long base, l
     }
 }
 
-// zero every entry that is not a degree of freedom
+// zero every entry that is not a degree of freedom, and the row padding
 template <typename T>
-__global__ void mask_kernel(int nx, int ny, int nz, T *e, T *h) {
-    const long long ncell = (long long)nx * ny * nz;
+__global__ void mask_kernel(int nx, int ny, int nz, int pitch, T *e, T *h) {
+    const long long ncell = (long long)pitch * ny * nz;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
          c += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(c % nx);
-        const int j = (int)((c / nx) % ny);
-        const int k = (int)(c / ((long long)nx * ny));
+        const int i = (int)(c % pitch);
+        const int j = (int)((c / pitch) % ny);
+        const int k = (int)(c / ((long long)pitch * ny));
+        const bool pad = i >= nx;
         if (e) {
-            if (j == 0 || k == 0) e[c] = T(0);
-            if (i == 0 || k == 0) e[ncell + c] = T(0);
-            if (i == 0 || j == 0) e[2 * ncell + c] = T(0);
+            if (pad || j == 0 || k == 0) e[c] = T(0);
+            if (pad || i == 0 || k == 0) e[ncell + c] = T(0);
+            if (pad || i == 0 || j == 0) e[2 * ncell + c] = T(0);
         }
         if (h) {
-            if (i == 0) h[c] = T(0);
-            if (j == 0) h[ncell + c] = T(0);
-            if (k == 0) h[2 * ncell + c] = T(0);
+            if (pad || i == 0) h[c] = T(0);
+            if (pad || j == 0) h[ncell + c] = T(0);
+            if (pad || k == 0) h[2 * ncell + c] = T(0);
         }
     }
 }
@@ -219,12 +221,6 @@ __global__ void sum_members_kernel(int nmem, long long len, const double *pm, lo
     }
 }
 
-template <typename Tin, typename Tout>
-__global__ void convert_kernel(long long n, const Tin *in, Tout *out) {
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
-         c += (long long)gridDim.x * blockDim.x)
-        out[c] = (Tout)in[c];
-}
 
 }  // namespace
 
@@ -254,12 +250,12 @@ cudaError_t check_materials(const float *eps, const float *mu, const float *sig,
 }
 
 template <typename T>
-cudaError_t build_coeffs(int nx, int ny, int nz, const double d[3], const float *eps, const float *mu,
+cudaError_t build_coeffs(int nx, int ny, int nz, int pitch, const double d[3], const float *eps, const float *mu,
                          const float *sig, double dt, int scheme, bool mu_array, T *ca, T *cb, T *ch, T *meps,
                          T *mmu, cudaStream_t s) {
-    const long long n = (long long)nx * ny * nz;
-    coeff_kernel<T><<<grid_for(n), kThreads, 0, s>>>(nx, ny, nz, d[0], d[1], d[2], eps, mu, sig, dt, scheme,
-                                                     mu_array ? 1 : 0, ca, cb, ch, meps, mmu);
+    const long long n = (long long)pitch * ny * nz;
+    coeff_kernel<T><<<grid_for(n), kThreads, 0, s>>>(nx, ny, nz, pitch, d[0], d[1], d[2], eps, mu, sig, dt,
+                                                     scheme, mu_array ? 1 : 0, ca, cb, ch, meps, mmu);
     return cudaGetLastError();
 }
 
@@ -271,8 +267,8 @@ cudaError_t source_table(const fit_source *src_dev, int nsrc, long long base, lo
 }
 
 template <typename T>
-cudaError_t mask_state(int nx, int ny, int nz, T *e, T *h, cudaStream_t s) {
-    mask_kernel<T><<<grid_for((long long)nx * ny * nz), kThreads, 0, s>>>(nx, ny, nz, e, h);
+cudaError_t mask_state(int nx, int ny, int nz, int pitch, T *e, T *h, cudaStream_t s) {
+    mask_kernel<T><<<grid_for((long long)pitch * ny * nz), kThreads, 0, s>>>(nx, ny, nz, pitch, e, h);
     return cudaGetLastError();
 }
 
@@ -299,28 +295,17 @@ cudaError_t sum_members(int nmem, long long len, const double *pm, long long str
     return cudaGetLastError();
 }
 
-template <typename Tin, typename Tout>
-cudaError_t convert_copy(long long n, const Tin *in, Tout *out, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    convert_kernel<Tin, Tout><<<grid_for(n), kThreads, 0, s>>>(n, in, out);
-    return cudaGetLastError();
-}
-
-template cudaError_t build_coeffs<float>(int, int, int, const double *, const float *, const float *,
+template cudaError_t build_coeffs<float>(int, int, int, int, const double *, const float *, const float *,
                                          const float *, double, int, bool, float *, float *, float *, float *,
                                          float *, cudaStream_t);
-template cudaError_t build_coeffs<double>(int, int, int, const double *, const float *, const float *,
+template cudaError_t build_coeffs<double>(int, int, int, int, const double *, const float *, const float *,
                                           const float *, double, int, bool, double *, double *, double *,
                                           double *, double *, cudaStream_t);
-template cudaError_t mask_state<float>(int, int, int, float *, float *, cudaStream_t);
-template cudaError_t mask_state<double>(int, int, int, double *, double *, cudaStream_t);
+template cudaError_t mask_state<float>(int, int, int, int, float *, float *, cudaStream_t);
+template cudaError_t mask_state<double>(int, int, int, int, double *, double *, cudaStream_t);
 template cudaError_t accumulate_state<float>(long long, const float *, double *, cudaStream_t);
 template cudaError_t accumulate_state<double>(long long, const double *, double *, cudaStream_t);
 template cudaError_t accumulate_state_kahan<float>(long long, const float *, float *, float *, cudaStream_t);
 template cudaError_t accumulate_state_kahan<double>(long long, const double *, float *, float *, cudaStream_t);
-template cudaError_t convert_copy<float, double>(long long, const float *, double *, cudaStream_t);
-template cudaError_t convert_copy<double, double>(long long, const double *, double *, cudaStream_t);
-template cudaError_t convert_copy<double, float>(long long, const double *, float *, cudaStream_t);
-template cudaError_t convert_copy<float, float>(long long, const float *, float *, cudaStream_t);
 
 }  // namespace fitgb

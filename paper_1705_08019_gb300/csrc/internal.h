@@ -1,12 +1,23 @@
 // internal.h -- declarations shared by the translation units of libfitgb.so.
 //
-// Device layout ("compact FIT layout", see include/fitgb.h): every field
-// component is an nx*ny*nz array, x fastest.  One leapfrog state is one block
-// of 6*ncell values: e_x, e_y, e_z, h_x, h_y, h_z.  Each member owns two such
-// blocks and the fused step reads one and writes the other (ping-pong), so
-// tiles never race on their halos.
+// Device layout.  Every field component and every per-edge/per-face
+// coefficient is a "pitched" array of pitch*ny*nz values: x fastest with the
+// row padded to pitch = nx rounded up to a multiple of 4, so every row starts
+// on a 16-byte boundary (the alignment TMA tensor copies need).  Padding
+// entries are zero and stay zero.  The ABI's compact layout (rows of nx) is
+// converted at the edges with 2-D copies.
+//
+// One leapfrog state is one block of 6 components: e_x, e_y, e_z, h_x, h_y,
+// h_z.  Each member owns two blocks and the fused step reads one and writes
+// the other (ping-pong), so tiles never race on their halos.  All member
+// blocks of a run sit in one allocation, block b of member q at index
+// 2q + b, so one 5-D tensor map (x, y, z, component, block) covers them all.
+//
+// Coefficients: one allocation of 3 or 6 components: cb_x, cb_y, cb_z and,
+// for lossy grids, ca_x, ca_y, ca_z (so one tensor copy brings both).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
@@ -26,13 +37,16 @@ constexpr int kMaxPrb = 32;   // probes fused into one step launch
 // Device error word bits.
 enum : int { kErrIndex = 1, kErrTimeout = 2 };
 
+inline int pitch_of(int nx) { return (nx + 3) & ~3; }
+
 struct EdgeRef {
     int axis, i, j, k;
 };
 
 // One leapfrog member: a state pair plus its place in absolute time.
 struct Member {
-    void *st[2];            // two 6*ncell state blocks (T)
+    void *st[2];            // the two 6-component state blocks (T)
+    int blk[2];             // their block indices in the run's state allocation
     long long start;        // absolute step of the member at iteration 0
     long long src_lo;       // sources act for absolute steps in [src_lo, src_hi)
     long long src_hi;
@@ -45,14 +59,14 @@ struct Member {
 // Arguments of one fused leapfrog launch (all members advance one step).
 template <typename T>
 struct StepArgs {
-    int nx, ny, nz;
-    long long ncell;
+    int nx, ny, nz, pitch;
+    long long ncell;        // pitch*ny*nz: the stride between components
     int tiles_x, tiles_y, nchunk, kz;
-    const T *ca;    // 3*ncell, or null when the grid is lossless (ca = 1)
-    const T *cb;    // 3*ncell
-    const T *ch;    // 3 values (uniform mu) or 3*ncell (per face)
-    const T *meps;  // 3*ncell, energy only
-    const T *mmu;   // 3 values or 3*ncell, energy only
+    const T *cb;    // 3 components
+    const T *ca;    // 3 components, or null when the grid is lossless (ca = 1)
+    const T *ch;    // 3 values (uniform mu) or 3 components (per face)
+    const T *meps;  // 3 components, energy only
+    const T *mmu;   // 3 values or 3 components, energy only
     const Member *mem;
     int nmem;       // members in this launch (table prefix)
     int it;         // iteration: member m is at absolute step mem[m].start + it
@@ -69,13 +83,27 @@ struct StepArgs {
 
 struct Tile {
     int tx, ty, kz;
+    int kernel;   // 1: shared-memory staging by plain loads, 2: TMA pipeline
 };
 
-// step.cu
+// step.cu: plain-load staging kernel
 template <typename T>
 cudaError_t launch_step(const StepArgs<T> &a, Tile tile, bool lossy, bool mu_array, bool energy,
                         cudaStream_t s);
 bool tile_supported(int tx, int ty);
+
+// step_tma.cu: TMA-pipelined kernel
+struct TmaMaps {
+    CUtensorMap state;   // (x, y, z, component, block), box (tx+8, ty+2, 1, 3, 1)
+    CUtensorMap coef;    // (x, y, z, component), box (tx, ty, 1, 3 or 6)
+};
+template <typename T>
+cudaError_t launch_step_tma(const StepArgs<T> &a, const TmaMaps &maps, Tile tile, bool lossy, bool mu_array,
+                            bool energy, cudaStream_t s);
+bool tma_tile_supported(int tx, int ty);
+// Encode the two tensor maps of a run; returns false if the driver lacks TMA.
+bool encode_tma_maps(TmaMaps *out, int elem_bytes, int nx, int ny, int nz, int pitch, void *state,
+                     int nblocks, const void *coef, int ncoef, int tx, int ty);
 
 // aux.cu
 struct MaterialFlags {
@@ -85,21 +113,19 @@ struct MaterialFlags {
 cudaError_t check_materials(const float *eps, const float *mu, const float *sig, long long ncell,
                             MaterialFlags *flags_host, void *scratch, cudaStream_t s);
 template <typename T>
-cudaError_t build_coeffs(int nx, int ny, int nz, const double d[3], const float *eps, const float *mu,
+cudaError_t build_coeffs(int nx, int ny, int nz, int pitch, const double d[3], const float *eps, const float *mu,
                          const float *sig, double dt, int scheme, bool mu_array, T *ca, T *cb, T *ch,
                          T *meps, T *mmu, cudaStream_t s);
 cudaError_t source_table(const fit_source *src_dev, int nsrc, long long base, long long len, double dt,
                          double *amp, cudaStream_t s);
 template <typename T>
-cudaError_t mask_state(int nx, int ny, int nz, T *e, T *h, cudaStream_t s);
+cudaError_t mask_state(int nx, int ny, int nz, int pitch, T *e, T *h, cudaStream_t s);
 template <typename T>
-cudaError_t accumulate_state(long long n6, const T *st, double *acc, cudaStream_t s);
+cudaError_t accumulate_state(long long n, const T *st, double *acc, cudaStream_t s);
 template <typename T>
-cudaError_t accumulate_state_kahan(long long n6, const T *st, float *sum, float *comp, cudaStream_t s);
+cudaError_t accumulate_state_kahan(long long n, const T *st, float *sum, float *comp, cudaStream_t s);
 cudaError_t kahan_finish(long long n, const float *sum, const float *comp, double *out, cudaStream_t s);
 cudaError_t sum_members(int nmem, long long len, const double *per_member, long long stride, double *out,
                         cudaStream_t s);
-template <typename Tin, typename Tout>
-cudaError_t convert_copy(long long n, const Tin *in, Tout *out, cudaStream_t s);
 
 }  // namespace fitgb

@@ -70,7 +70,8 @@ __global__ void __launch_bounds__(TX *TY) step_kernel(const StepArgs<T> a) {
 
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const long long ncell = a.ncell;
-    const long long plane = (long long)nx * ny;
+    const int pitch = a.pitch;
+    const long long plane = (long long)pitch * ny;
     const int i0 = tile_x * TX, j0 = tile_y * TY;
     const int i = i0 + lx, j = j0 + ly;
     const bool own = (i < nx) && (j < ny);
@@ -138,7 +139,7 @@ __global__ void __launch_bounds__(TX *TY) step_kernel(const StepArgs<T> a) {
             const int gi = i0 - 1 + ii, gj = j0 - 1 + jj;                                   \
             T vx = T(0), vy = T(0), vz = T(0);                                              \
             if (kin_ && gi >= 0 && gi < nx && gj >= 0 && gj < ny) {                         \
-                const long long c_ = (long long)(kk) * plane + (long long)gj * nx + gi;     \
+                const long long c_ = (long long)(kk) * plane + (long long)gj * pitch + gi;     \
                 vx = iex[c_];                                                               \
                 vy = iey[c_];                                                               \
                 vz = iez[c_];                                                               \
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(TX *TY) step_kernel(const StepArgs<T> a) {
         const int cur = k & 1, nxt = cur ^ 1;
         FIT_LOAD_PLANE(nxt, k + 1);
 
-        const long long c = (long long)k * plane + (long long)j * nx + i;
+        const long long c = (long long)k * plane + (long long)j * pitch + i;
         T ho[3] = {T(0), T(0), T(0)};
         if (own) {
             ho[0] = ihx[c];
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(TX *TY) step_kernel(const StepArgs<T> a) {
             if (hx_col) { hi = i0 - 1; hj = j0 + tid; }
             if (hy_row) { hi = i0 + tid - TY; hj = j0 - 1; }
             if (hi >= 0 && hj >= 0 && hi < nx && hj < ny) {
-                const long long hc = (long long)k * plane + (long long)hj * nx + hi;
+                const long long hc = (long long)k * plane + (long long)hj * pitch + hi;
                 if (hx_col) { hh0 = ihy[hc]; hh1 = ihz[hc]; }   // h_y, h_z
                 else        { hh0 = ihx[hc]; hh1 = ihz[hc]; }   // h_x, h_z
             } else {
@@ -216,7 +217,7 @@ __global__ void __launch_bounds__(TX *TY) step_kernel(const StepArgs<T> a) {
                 T v0 = T(0), v1 = T(0);
                 if (hi >= 0) {
                     const int qx = hi - i0 + 1, qy = hj - j0 + 1;   // region coords
-                    long long hc = (long long)k * plane + (long long)hj * nx + hi;
+                    long long hc = (long long)k * plane + (long long)hj * pitch + hi;
                     if (hx_col) {
                         const T cyh = sE[cur][2][qy][qx] + sE[nxt][0][qy][qx] - sE[cur][2][qy][qx + 1]
                                       - sE[cur][0][qy][qx];

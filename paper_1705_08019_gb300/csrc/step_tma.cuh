@@ -1,0 +1,420 @@
+// step_tma.cuh -- the fused FIT leapfrog step (Sec. II-A of the paper) with a
+// TMA pipeline: the GB300 path of the hot loop.
+//
+// One CTA owns a TX x TY column of cells of one member and streams it along z
+// over a chunk of planes (2.5-D blocking).  Plane data arrives by TMA
+// (cp.async.bulk.tensor) into an S-deep shared-memory ring, one stage per
+// plane, completing on one mbarrier per stage:
+//   e^n       of the plane, x in [i0-4, i0+TX+4), y in [j0-1, j0+TY+1)
+//   h^{n-1/2} of the plane, same window
+//   cb (and ca) of the plane's TX x TY cells
+// The e/h window starts 4 cells left of the tile so that its x coordinate is
+// 16-byte aligned, as TMA requires; cells outside the grid arrive as zeros
+// (the tensor maps' out-of-bounds fill), which is exactly the PEC/ghost
+// value, so no bounds test is needed on the loads.  Thread 0 keeps S planes
+// in flight, so DRAM latency hides behind the compute of earlier planes.
+//
+// Per plane k every thread computes h^{n+1/2} = h^{n-1/2} - ch (C e^n) for its
+// cell (and the first TX+TY threads also for the low-x column / low-y row
+// next to the tile, whose values its neighbours' e updates need), then
+// e^{n+1} = ca e^n + cb (C~h^{n+1/2} - j^{n+1/2}) using the shared h plane and
+// the previous plane's h_x, h_y kept in registers.  Fields are written with
+// coalesced stores into the member's other state block.  Every byte of e, h
+// and the coefficients is read once from DRAM per step (halo re-reads come
+// from L2) and every field value is written once.
+//
+// Sources, probes and the interleaved energy W^n (eq. energy) are fused as in
+// the plain-load kernel.  Every mbarrier wait is bounded: on timeout the CTA
+// records kErrTimeout, stops, waits (bounded) for its own copies in flight
+// and returns.
+#pragma once
+
+#include "internal.h"
+
+namespace fitgb {
+namespace tma {
+
+constexpr int kWaitLimit = 1 << 22;
+
+__device__ __forceinline__ uint32_t saddr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void proxy_fence() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(saddr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (int n = 0; n < kWaitLimit; ++n)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
+                                            int c2, int c3, int c4) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(saddr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(saddr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
+                                            int c2, int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(saddr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(saddr(bar))
+        : "memory");
+}
+
+constexpr int align128(int b) { return (b + 127) & ~127; }
+
+template <typename T>
+struct Acc;
+template <>
+struct Acc<float> {   // Kahan-compensated FP32
+    float s = 0.f, c = 0.f;
+    __device__ void add(float x) {
+        float y = x - c;
+        float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ double value() const { return (double)s - (double)c; }
+};
+template <>
+struct Acc<double> {
+    double s = 0.0;
+    __device__ void add(double x) { s += x; }
+    __device__ double value() const { return s; }
+};
+
+template <typename T, int TX, int TY, int S, bool LOSSY>
+struct Geometry {
+    static constexpr int NT = TX * TY;
+    static constexpr int BX = TX + 8;   // e/h window width: 4 cells each side
+    static constexpr int EY = TY + 2;   // e/h window height: 1 row each side
+    static constexpr int NC = LOSSY ? 6 : 3;
+    static constexpr int E_BYTES = 3 * EY * BX * (int)sizeof(T);
+    static constexpr int C_BYTES = NC * TY * TX * (int)sizeof(T);
+    static constexpr int H_OFF = align128(E_BYTES);
+    static constexpr int C_OFF = H_OFF + align128(E_BYTES);
+    static constexpr int STAGE = C_OFF + align128(C_BYTES);
+    static constexpr uint32_t TX_BYTES = 2 * E_BYTES + C_BYTES;
+    static constexpr int DYN_SMEM = S * STAGE;
+};
+
+template <typename T, int TX, int TY, int S, bool LOSSY>
+__global__ void __launch_bounds__(TX *TY) step_tma_kernel(const StepArgs<T> a, const __grid_constant__ CUtensorMap tm_state,
+                                                          const __grid_constant__ CUtensorMap tm_coef, int muarr,
+                                                          int energy) {
+    using G = Geometry<T, TX, TY, S, LOSSY>;
+    constexpr int NT = G::NT, BX = G::BX, EY = G::EY;
+    static_assert(S >= 3, "the e plane k+1 is read while plane k+S is in flight");
+    static_assert(TX + TY <= NT, "halo threads");
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ __align__(8) uint64_t bar[S];
+    __shared__ T sH[3][TY + 1][TX + 1];   // h^{n+1/2} of plane k with low halos
+    __shared__ EdgeRef sSrcRef[kMaxSrc], sPrbRef[kMaxPrb];
+    __shared__ int sSrc[kMaxSrc], sPrb[kMaxPrb];
+    __shared__ int sNsrc, sNprb;
+    __shared__ double sRed[NT / 32];
+
+    const int tid = threadIdx.x;
+    const int lx = tid % TX, ly = tid / TX;
+
+    int rest = blockIdx.x;   // CTA -> (member, tile, z chunk), member fastest
+    const int m = rest % a.nmem;
+    rest /= a.nmem;
+    const int tile_x = rest % a.tiles_x;
+    rest /= a.tiles_x;
+    const int tile_y = rest % a.tiles_y;
+    const int chunk = rest / a.tiles_y;
+
+    const int nx = a.nx, ny = a.ny, nz = a.nz, pitch = a.pitch;
+    const long long ncell = a.ncell;
+    const int i0 = tile_x * TX, j0 = tile_y * TY;
+    const int i = i0 + lx, j = j0 + ly;
+    const bool own = (i < nx) && (j < ny);
+    const int k0 = chunk * a.kz;
+    const int k1 = min(nz, k0 + a.kz);
+    const int kstart = (k0 > 0) ? k0 - 1 : k0;   // k0-1: prologue plane (h only)
+    const int total = k1 - kstart + 1;            // planes kstart .. k1
+
+    const Member mb = a.mem[m];
+    const long long step = mb.start + a.it;
+    const int blk_in = a.parity ? mb.blk[1] : mb.blk[0];
+    T *__restrict__ out = static_cast<T *>(a.parity ? mb.st[0] : mb.st[1]);
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
+        mbar_init_fence();
+        int ns = 0, np = 0;
+        const bool on = step >= mb.src_lo && step < mb.src_hi;
+#pragma unroll
+        for (int s = 0; s < kMaxSrc; ++s) {
+            const EdgeRef r = a.src[s];
+            if (on && s < a.nsrc && r.i >= i0 && r.i < i0 + TX && r.j >= j0 && r.j < j0 + TY && r.k >= k0 &&
+                r.k < k1) {
+                sSrc[ns] = s;
+                sSrcRef[ns] = r;
+                ++ns;
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < kMaxPrb; ++p) {
+            const EdgeRef r = a.prb[p];
+            if (mb.probe && p < a.nprb && r.i >= i0 && r.i < i0 + TX && r.j >= j0 && r.j < j0 + TY &&
+                r.k >= k0 && r.k < k1) {
+                sPrb[np] = p;
+                sPrbRef[np] = r;
+                ++np;
+            }
+        }
+        sNsrc = ns;
+        sNprb = np;
+    }
+    __syncthreads();
+
+    auto issue = [&](int p) {   // thread 0: start the copies of plane kstart + p
+        const int kk = kstart + p;
+        unsigned char *st = dsm + (p % S) * G::STAGE;
+        uint64_t *b = &bar[p % S];
+        mbar_expect_tx(b, G::TX_BYTES);
+        tma_load_5d(st, &tm_state, b, i0 - 4, j0 - 1, kk, 0, blk_in);
+        tma_load_5d(st + G::H_OFF, &tm_state, b, i0 - 4, j0 - 1, kk, 3, blk_in);
+        tma_load_4d(st + G::C_OFF, &tm_coef, b, i0, j0, kk, 0);
+    };
+    int issued = 0;
+    if (tid == 0) {
+        for (; issued < min(S, total); ++issued) issue(issued);
+    }
+
+    T ch[3] = {T(0), T(0), T(0)};
+    if (!muarr) {
+        ch[0] = a.ch[0];
+        ch[1] = a.ch[1];
+        ch[2] = a.ch[2];
+    }
+    T mmu_c[3] = {T(0), T(0), T(0)};
+    if (energy && !muarr) {
+        mmu_c[0] = a.mmu[0];
+        mmu_c[1] = a.mmu[1];
+        mmu_c[2] = a.mmu[2];
+    }
+    const bool hx_col = tid < TY;                  // low-x halo column
+    const bool hy_row = tid >= TY && tid < TY + TX; // low-y halo row
+    T hxp = T(0), hyp = T(0);   // h_x, h_y at (i, j, k-1), step n+1/2
+    Acc<T> wacc;
+    int bad = mbar_wait(&bar[0], 0) ? 0 : 1;
+    int waited = bad ? 0 : 1;   // planes whose copies are known complete
+    bool aborted = false;
+
+    for (int k = kstart; k < k1; ++k) {
+        const int p = k - kstart;
+        const bool pro = k < k0;
+        const T *eC = reinterpret_cast<const T *>(dsm + (p % S) * G::STAGE);
+        const T *hC = reinterpret_cast<const T *>(dsm + (p % S) * G::STAGE + G::H_OFF);
+        const T *cC = reinterpret_cast<const T *>(dsm + (p % S) * G::STAGE + G::C_OFF);
+        const T *eN = reinterpret_cast<const T *>(dsm + ((p + 1) % S) * G::STAGE);
+        if (!bad) {
+            if (mbar_wait(&bar[(p + 1) % S], ((p + 1) / S) & 1)) waited = p + 2;
+            else bad = 1;
+        }
+#define EV(buf, comp, y, x) (buf)[((comp) * EY + (y)) * BX + (x)]
+        const int sx = lx + 4, sy = ly + 1;
+        const long long c = ((long long)k * ny + j) * pitch + i;
+        T chl0 = ch[0], chl1 = ch[1], chl2 = ch[2];
+        if (muarr) {
+            chl0 = own ? a.ch[c] : T(0);
+            chl1 = own ? a.ch[ncell + c] : T(0);
+            chl2 = own ? a.ch[2 * ncell + c] : T(0);
+        }
+        const T ex0 = EV(eC, 0, sy, sx), ey0 = EV(eC, 1, sy, sx), ez0 = EV(eC, 2, sy, sx);
+        const T ho0 = EV(hC, 0, sy, sx), ho1 = EV(hC, 1, sy, sx), ho2 = EV(hC, 2, sy, sx);
+        // (C e)_x = e_y(q) + e_z(q+y) - e_y(q+z) - e_z(q)
+        const T cx = ey0 + EV(eC, 2, sy + 1, sx) - EV(eN, 1, sy, sx) - ez0;
+        // (C e)_y = e_z(q) + e_x(q+z) - e_z(q+x) - e_x(q)
+        const T cy = ez0 + EV(eN, 0, sy, sx) - EV(eC, 2, sy, sx + 1) - ex0;
+        // (C e)_z = e_x(q) + e_y(q+x) - e_x(q+y) - e_y(q)
+        const T cz = ex0 + EV(eC, 1, sy, sx + 1) - EV(eC, 0, sy + 1, sx) - ey0;
+        const T hxn = ho0 - chl0 * cx;
+        const T hyn = ho1 - chl1 * cy;
+        const T hzn = ho2 - chl2 * cz;
+        if (!pro) {
+            sH[0][sy][lx + 1] = hxn;
+            sH[1][sy][lx + 1] = hyn;
+            sH[2][sy][lx + 1] = hzn;
+            if (hx_col) {   // cell (i0-1, j0+tid): window x = 3
+                const int y = tid + 1;
+                T c1 = ch[1], c2 = ch[2];
+                if (muarr) {
+                    const int hi = i0 - 1, hj = j0 + tid;
+                    const bool in = hi >= 0 && hj < ny;
+                    const long long hc = ((long long)k * ny + hj) * pitch + hi;
+                    c1 = in ? a.ch[ncell + hc] : T(0);
+                    c2 = in ? a.ch[2 * ncell + hc] : T(0);
+                }
+                const T cyh = EV(eC, 2, y, 3) + EV(eN, 0, y, 3) - EV(eC, 2, y, 4) - EV(eC, 0, y, 3);
+                const T czh = EV(eC, 0, y, 3) + EV(eC, 1, y, 4) - EV(eC, 0, y + 1, 3) - EV(eC, 1, y, 3);
+                sH[1][y][0] = EV(hC, 1, y, 3) - c1 * cyh;
+                sH[2][y][0] = EV(hC, 2, y, 3) - c2 * czh;
+            } else if (hy_row) {   // cell (i0+t, j0-1): window y = 0
+                const int t = tid - TY, x = t + 4;
+                T c0 = ch[0], c2 = ch[2];
+                if (muarr) {
+                    const int hi = i0 + t, hj = j0 - 1;
+                    const bool in = hj >= 0 && hi < nx;
+                    const long long hc = ((long long)k * ny + hj) * pitch + hi;
+                    c0 = in ? a.ch[hc] : T(0);
+                    c2 = in ? a.ch[2 * ncell + hc] : T(0);
+                }
+                const T cxh = EV(eC, 1, 0, x) + EV(eC, 2, 1, x) - EV(eN, 1, 0, x) - EV(eC, 2, 0, x);
+                const T czh = EV(eC, 0, 0, x) + EV(eC, 1, 0, x + 1) - EV(eC, 0, 1, x) - EV(eC, 1, 0, x);
+                sH[0][0][t + 1] = EV(hC, 0, 0, x) - c0 * cxh;
+                sH[2][0][t + 1] = EV(hC, 2, 0, x) - c2 * czh;
+            }
+            if (own) {
+                out[3 * ncell + c] = hxn;
+                out[4 * ncell + c] = hyn;
+                out[5 * ncell + c] = hzn;
+            }
+        }
+#undef EV
+        if (__syncthreads_or(bad)) {   // (B) h plane complete
+            aborted = true;
+            break;
+        }
+        if (!pro && own) {
+            const int sxh = lx + 1;
+            // (C~h)_x = h_z(q) - h_z(q-y) - h_y(q) + h_y(q-z)
+            T tx = hzn - sH[2][sy - 1][sxh] - hyn + hyp;
+            // (C~h)_y = h_x(q) - h_x(q-z) - h_z(q) + h_z(q-x)
+            T ty = hxn - hxp - hzn + sH[2][sy][sxh - 1];
+            // (C~h)_z = h_y(q) - h_y(q-x) - h_x(q) + h_x(q-y)
+            T tz = hyn - sH[1][sy][sxh - 1] - hxn + sH[0][sy - 1][sxh];
+            for (int q = 0; q < sNsrc; ++q) {
+                const EdgeRef r = sSrcRef[q];
+                if (r.i == i && r.j == j && r.k == k) {
+                    const T jv = (T)a.amp[(step - a.amp_base) * a.nsrc + sSrc[q]];
+                    if (r.axis == 0) tx -= jv;
+                    else if (r.axis == 1) ty -= jv;
+                    else tz -= jv;
+                }
+            }
+            const int cc = ly * TX + lx;
+            const T bx = cC[cc], by = cC[TY * TX + cc], bz = cC[2 * TY * TX + cc];
+            T exn, eyn, ezn;
+            if (LOSSY) {
+                exn = cC[3 * TY * TX + cc] * ex0 + bx * tx;
+                eyn = cC[4 * TY * TX + cc] * ey0 + by * ty;
+                ezn = cC[5 * TY * TX + cc] * ez0 + bz * tz;
+            } else {
+                exn = ex0 + bx * tx;
+                eyn = ey0 + by * ty;
+                ezn = ez0 + bz * tz;
+            }
+            out[c] = exn;
+            out[ncell + c] = eyn;
+            out[2 * ncell + c] = ezn;
+            for (int q = 0; q < sNprb; ++q) {
+                const EdgeRef r = sPrbRef[q];
+                if (r.i == i && r.j == j && r.k == k) {
+                    const T v = r.axis == 0 ? exn : (r.axis == 1 ? eyn : ezn);
+                    mb.probe[(step - mb.probe_base) * a.nprb + sPrb[q]] = (double)v;
+                }
+            }
+            if (energy) {
+                const T me0 = a.meps[c], me1 = a.meps[ncell + c], me2 = a.meps[2 * ncell + c];
+                T mu0 = mmu_c[0], mu1 = mmu_c[1], mu2 = mmu_c[2];
+                if (muarr) {
+                    mu0 = a.mmu[c];
+                    mu1 = a.mmu[ncell + c];
+                    mu2 = a.mmu[2 * ncell + c];
+                }
+                wacc.add(me0 * ex0 * ex0);
+                wacc.add(me1 * ey0 * ey0);
+                wacc.add(me2 * ez0 * ez0);
+                wacc.add(mu0 * ho0 * hxn);
+                wacc.add(mu1 * ho1 * hyn);
+                wacc.add(mu2 * ho2 * hzn);
+            }
+        }
+        hxp = hxn;
+        hyp = hyn;
+        __syncthreads();   // (C) stage p and the h plane are free again
+        if (tid == 0 && issued < total) {
+            proxy_fence();
+            issue(issued);
+            ++issued;
+        }
+    }
+
+    if (aborted) {
+        if (tid == 0) {
+            atomicOr(a.err, kErrTimeout);
+            // do not leave while copies into this CTA's shared memory are pending
+            for (int p = waited; p < issued; ++p) mbar_wait(&bar[p % S], (p / S) & 1);
+        }
+        return;
+    }
+    if (energy) {
+        double v = wacc.value();
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if ((tid & 31) == 0) sRed[tid >> 5] = v;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < NT / 32; ++w) t += sRed[w];
+            if (mb.energy) atomicAdd(mb.energy + (step - mb.energy_base), t);
+        }
+    }
+}
+
+template <typename T, int TX, int TY, int S, bool LOSSY>
+cudaError_t launch_one(const StepArgs<T> &a, const TmaMaps &maps, bool muarr, bool energy, cudaStream_t s) {
+    using G = Geometry<T, TX, TY, S, LOSSY>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(step_tma_kernel<T, TX, TY, S, LOSSY>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, G::DYN_SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const long long blocks = (long long)a.nmem * a.tiles_x * a.tiles_y * a.nchunk;
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    step_tma_kernel<T, TX, TY, S, LOSSY><<<(unsigned)blocks, TX * TY, G::DYN_SMEM, s>>>(
+        a, maps.state, maps.coef, muarr ? 1 : 0, energy ? 1 : 0);
+    return cudaGetLastError();
+}
+
+}  // namespace tma
+}  // namespace fitgb

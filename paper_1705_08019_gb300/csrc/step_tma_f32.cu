@@ -1,0 +1,74 @@
+// step_tma_f32.cu -- FP32 instantiations of the TMA-pipelined step and the
+// tensor-map encoder.
+#include <cudaTypedefs.h>
+
+#include "step_tma.cuh"
+
+namespace fitgb {
+
+bool tma_tile_supported(int tx, int ty) {
+    return (tx == 32 && (ty == 4 || ty == 8 || ty == 16)) || (tx == 64 && ty == 4);
+}
+
+template <>
+cudaError_t launch_step_tma<float>(const StepArgs<float> &a, const TmaMaps &maps, Tile t, bool lossy, bool muarr,
+                                   bool energy, cudaStream_t s) {
+    using namespace tma;
+#define FIT_T(TX, TY, S)                                                                   \
+    if (t.tx == TX && t.ty == TY)                                                          \
+        return lossy ? launch_one<float, TX, TY, S, true>(a, maps, muarr, energy, s)       \
+                     : launch_one<float, TX, TY, S, false>(a, maps, muarr, energy, s);
+    FIT_T(32, 8, 4)
+    FIT_T(32, 16, 3)
+    FIT_T(32, 4, 4)
+    FIT_T(64, 4, 4)
+#undef FIT_T
+    return cudaErrorInvalidValue;
+}
+
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+}  // namespace
+
+bool encode_tma_maps(TmaMaps *out, int eb, int nx, int ny, int nz, int pitch, void *state, int nblocks,
+                     const void *coef, int ncoef, int tx, int ty) {
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encoder();
+    if (!fn) return false;
+    const CUtensorMapDataType dt = eb == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    const cuuint64_t row = (cuuint64_t)pitch * eb;
+    const cuuint64_t plane = row * ny;
+    const cuuint64_t comp = plane * nz;
+    cuuint64_t sdim[5] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, 6, (cuuint64_t)nblocks};
+    cuuint64_t sstr[4] = {row, plane, comp, 6 * comp};
+    cuuint32_t sbox[5] = {(cuuint32_t)(tx + 8), (cuuint32_t)(ty + 2), 1, 3, 1};
+    cuuint32_t ones[5] = {1, 1, 1, 1, 1};
+    if (fn(&out->state, dt, 5, state, sdim, sstr, sbox, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+        return false;
+    cuuint64_t cdim[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)ncoef};
+    cuuint64_t cstr[3] = {row, plane, comp};
+    cuuint32_t cbox[4] = {(cuuint32_t)tx, (cuuint32_t)ty, 1, (cuuint32_t)ncoef};
+    if (fn(&out->coef, dt, 4, const_cast<void *>(coef), cdim, cstr, cbox, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+        return false;
+    return true;
+}
+
+}  // namespace fitgb

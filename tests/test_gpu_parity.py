@@ -110,8 +110,9 @@ SHAPES = [
 ]
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
 @pytest.mark.parametrize("dims,kw", SHAPES)
-def test_leapfrog_fp32_matches_oracle(dims, kw):
+def test_leapfrog_fp32_matches_oracle(dims, kw, kernel):
     w = W.small_random(dims=dims, nsteps=300, **kw)
     if dims[2] == 1:
         w.sources = [dict(w.sources[0], axis=2, k=0)]
@@ -119,7 +120,7 @@ def test_leapfrog_fp32_matches_oracle(dims, kw):
     if dims[0] == 1:
         w.sources = [dict(w.sources[0], axis=0, i=0, j=3, k=3)]
         w.probes = [dict(axis=0, i=0, j=2, k=5), dict(axis=0, i=0, j=4, k=1)]
-    gpu, ref, tol = run_pair(w, w.nsteps, 32)
+    gpu, ref, tol = run_pair(w, w.nsteps, 32, opts=fitgb.make_opts(kernel=kernel))
     check_pair(gpu, ref, tol)
 
 
@@ -219,9 +220,11 @@ def test_tiles_agree():
     dt = w.cfl_fraction * oracle.cfl_dt(w.dims, w.spacing, w.eps_r)
     g = fitgb.Grid.from_workload(w, 32)
     ref = None
-    for tx, ty, tz in [(32, 8, 8), (32, 4, 16), (32, 16, 0), (64, 4, 5), (64, 2, 7), (16, 8, 3)]:
+    combos = [(1, 32, 8, 8), (1, 32, 4, 16), (1, 32, 16, 0), (1, 64, 4, 5), (1, 64, 2, 7), (1, 16, 8, 3),
+              (2, 32, 8, 8), (2, 32, 4, 16), (2, 32, 16, 0), (2, 64, 4, 5), (2, 32, 8, 1)]
+    for kern, tx, ty, tz in combos:
         out = g.leapfrog(dt, w.nsteps, w.sources, w.probes, energy=True,
-                         opts=fitgb.make_opts(tile_x=tx, tile_y=ty, tile_z=tz))
+                         opts=fitgb.make_opts(tile_x=tx, tile_y=ty, tile_z=tz, kernel=kern))
         if ref is None:
             ref = out
             continue
