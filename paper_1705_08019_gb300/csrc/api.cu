@@ -170,7 +170,7 @@ Tile pick_tile(const fit_grid *g, const fit_run_opts *o) {
         t.tx = o->tile_x;
         t.ty = o->tile_y;
     }
-    if (t.kernel == 2 && !tma_tile_supported(t.tx, t.ty)) t.kernel = 1;
+    if (t.kernel == 2 && !tma_tile_supported(t.tx, t.ty, g->prec == 64 ? 8 : 4)) t.kernel = 1;
     if (t.kernel == 1 && !tile_supported(t.tx, t.ty)) {
         t.tx = 32;
         t.ty = 8;

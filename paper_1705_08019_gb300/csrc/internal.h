@@ -100,7 +100,7 @@ struct TmaMaps {
 template <typename T>
 cudaError_t launch_step_tma(const StepArgs<T> &a, const TmaMaps &maps, Tile tile, bool lossy, bool mu_array,
                             bool energy, cudaStream_t s);
-bool tma_tile_supported(int tx, int ty);
+bool tma_tile_supported(int tx, int ty, int elem_bytes);
 // Encode the two tensor maps of a run; returns false if the driver lacks TMA.
 bool encode_tma_maps(TmaMaps *out, int elem_bytes, int nx, int ny, int nz, int pitch, void *state,
                      int nblocks, const void *coef, int ncoef, int tx, int ty);

@@ -128,7 +128,7 @@ struct Geometry {
     static constexpr int C_OFF = H_OFF + align128(E_BYTES);
     static constexpr int STAGE = C_OFF + align128(C_BYTES);
     static constexpr uint32_t TX_BYTES = 2 * E_BYTES + C_BYTES;
-    static constexpr int DYN_SMEM = S * STAGE;
+    static constexpr int DYN_SMEM = S * STAGE + 128;   // + room to align the base to 128 B
 };
 
 template <typename T, int TX, int TY, int S, bool LOSSY>
@@ -139,7 +139,9 @@ __global__ void __launch_bounds__(TX *TY) step_tma_kernel(const StepArgs<T> a, c
     constexpr int NT = G::NT, BX = G::BX, EY = G::EY;
     static_assert(S >= 3, "the e plane k+1 is read while plane k+S is in flight");
     static_assert(TX + TY <= NT, "halo threads");
-    extern __shared__ __align__(128) unsigned char dsm[];
+    extern __shared__ __align__(128) unsigned char dsm_raw[];
+    unsigned char *dsm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(dsm_raw) + 127) &
+                                                           ~static_cast<uintptr_t>(127));
     __shared__ __align__(8) uint64_t bar[S];
     __shared__ T sH[3][TY + 1][TX + 1];   // h^{n+1/2} of plane k with low halos
     __shared__ EdgeRef sSrcRef[kMaxSrc], sPrbRef[kMaxPrb];

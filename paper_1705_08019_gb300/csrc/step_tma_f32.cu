@@ -6,7 +6,8 @@
 
 namespace fitgb {
 
-bool tma_tile_supported(int tx, int ty) {
+bool tma_tile_supported(int tx, int ty, int elem_bytes) {
+    if (elem_bytes == 8) return tx == 32 && (ty == 4 || ty == 8);
     return (tx == 32 && (ty == 4 || ty == 8 || ty == 16)) || (tx == 64 && ty == 4);
 }
 
