@@ -218,6 +218,30 @@ int fit_adjoint_grad(fit_grid *g, double dt, long nsteps,
 /* Counters of the last run on `g` (see fit_run_stats). */
 int fit_last_stats(const fit_grid *g, fit_run_stats *out);
 
+/* FP32 leapfrog run that allocates no device memory, for callers that cannot
+ * call cudaMalloc (a fixed memory budget handed out up front, a real-time loop
+ * where an allocation may block or fail, a plugin that must not grow the
+ * process's footprint).  The paper has no counterpart: this is a deployment
+ * variant of fit_leapfrog_run for mu_r = 1 and the semi-implicit sigma scheme,
+ * without energy output.
+ *   eps_r, sigma (NULL = 0): device, nx*ny*nz per-cell values.
+ *   e_io, h_io: device, 3*nx*ny*nz floats each (compact layout), the initial
+ *     state on entry and the final one on exit (both required).
+ *   probe_out: device, nsteps*nprb doubles, or NULL.  src, prb: host arrays.
+ * Every workspace lives in one fixed __device__ array of about 30 MiB held
+ * by each GPU that loads the library until the process exits, so grids are
+ * limited to ceil4(nx)*ny*nz <= 393216 cells (e.g. 64 x 64 x 96); larger
+ * grids, more than 8 sources or 32 probes, or host pointers give
+ * FIT_ERR_ARG.  The first call on a device looks the array up
+ * (cudaGetSymbolAddress) and should come before any stream capture.  All
+ * calls share the array: calls whose work overlaps on the GPU race on it and
+ * must be serialized by the caller.  Returns after the run has finished
+ * (FIT_ERR_CFL / FIT_ERR_NONFINITE as fit_leapfrog_run). */
+int fit_leapfrog_run_static(int nx, int ny, int nz, double dx, double dy, double dz,
+                            const float *eps_r, const float *sigma, double dt, long nsteps, long step0,
+                            const fit_source *src, int nsrc, const fit_probe *prb, int nprb,
+                            double *probe_out, float *e_io, float *h_io, void *stream);
+
 /* Wait for the grid's outstanding work on `stream` and return the first
  * deferred device error, if any. */
 int fit_sync(fit_grid *g, void *stream);

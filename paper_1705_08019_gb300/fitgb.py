@@ -30,7 +30,7 @@ WAVE_GAUSS_SINE, WAVE_GAUSS, WAVE_SINE = 0, 1, 2
 
 EXPORTED = ("fit_grid_create", "fit_grid_destroy", "fit_cfl_dt", "fit_grid_info", "fit_leapfrog_run",
             "paraexp_run", "paraexp_run_batched", "fit_adjoint_grad", "fit_sync", "fit_strerror",
-            "fit_version", "fit_last_stats")
+            "fit_version", "fit_last_stats", "fit_leapfrog_run_static")
 
 
 class FitError(RuntimeError):
@@ -99,6 +99,8 @@ def load():
         lib.paraexp_run_batched.restype = I
         lib.fit_adjoint_grad.argtypes = [P, D, L, P, I, P, I, I, P, P, P, P]
         lib.fit_adjoint_grad.restype = I
+        lib.fit_leapfrog_run_static.argtypes = [I, I, I, D, D, D, P, P, D, L, L, P, I, P, I, P, P, P, P]
+        lib.fit_leapfrog_run_static.restype = I
         lib.fit_last_stats.argtypes = [P, ctypes.POINTER(fit_run_stats)]
         lib.fit_last_stats.restype = I
         lib.fit_sync.argtypes = [P, P]
@@ -269,6 +271,19 @@ def fit_adjoint_grad(g, dt, nsteps, sources=(), probes=(), ckpt_every=0, J_out=N
                                  _addr(grad_out), ctypes.byref(opts) if opts is not None else None,
                                  _stream(stream))
     _check(rc, "fit_adjoint_grad")
+
+
+def fit_leapfrog_run_static(dims, spacing, eps_r, sigma, dt, nsteps, step0=0, sources=(), probes=(),
+                            probe_out=None, e_io=None, h_io=None, stream=None):
+    """The allocation-free FP32 leapfrog run; every array argument is a
+    device tensor (e_io, h_io: float32, shape (3, nz, ny, nx), in/out)."""
+    nx, ny, nz = (int(v) for v in dims)
+    src, prb = sources_array(sources), probes_array(probes)
+    rc = load().fit_leapfrog_run_static(nx, ny, nz, *(float(v) for v in spacing), _addr(eps_r), _addr(sigma),
+                                        float(dt), int(nsteps), int(step0), ctypes.cast(src, ctypes.c_void_p),
+                                        len(sources), ctypes.cast(prb, ctypes.c_void_p), len(probes),
+                                        _addr(probe_out), _addr(e_io), _addr(h_io), _stream(stream))
+    _check(rc, "fit_leapfrog_run_static")
 
 
 def fit_last_stats(g):
