@@ -128,4 +128,18 @@ cudaError_t kahan_finish(long long n, const float *sum, const float *comp, doubl
 cudaError_t sum_members(int nmem, long long len, const double *per_member, long long stride, double *out,
                         cudaStream_t s);
 
+// adjoint.cu
+template <typename T>
+cudaError_t adjoint_init(const fit_probe *prb, int nprb, const double d[3], const double *probe_last, const T *cb,
+                         T *mu, int pitch, int ny, long long ncp, cudaStream_t s);
+cudaError_t adjoint_sources(const fit_probe *prb, int nprb, const double d[3], const double *probe, long long N,
+                            double *amp, cudaStream_t s);
+template <typename T>
+cudaError_t grad_accumulate(long long ncp, const T *mu, const T *e1, const T *e0, const double k[3], double *g,
+                            cudaStream_t s);
+cudaError_t grad_scatter(int nx, int ny, int nz, int pitch, long long ncp, const double *g, double *grad,
+                         cudaStream_t s);
+cudaError_t probe_functional(const fit_probe *prb, int nprb, const double d[3], const double *probe, long long N,
+                             double *J, cudaStream_t s);
+
 }  // namespace fitgb
