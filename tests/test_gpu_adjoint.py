@@ -128,15 +128,12 @@ def test_fullsize_adjoint128_central_fd():
     assert np.isfinite(grad).all() and J > 0
     L = np.array([w.spacing[p["axis"]] for p in w.probes])
 
-    g64 = fitgb.Grid(w.dims, w.spacing, w.eps_r, None, w.sigma, 64)
-
     def J_of(eps):
         gg = fitgb.Grid(w.dims, w.spacing, eps, None, w.sigma, 64)
         pr, _, _, _ = gg.leapfrog(dt, w.nsteps, w.sources, w.probes, opts=fitgb.make_opts(force_dt=1))
         gg.close()
         return float(np.sum((pr / L) ** 2))
 
-    g64.close()
     fd, ad = [], []
     for k, j, i in W.fd_cells(w):
         ep, em = w.eps_r.copy(), w.eps_r.copy()
@@ -146,3 +143,24 @@ def test_fullsize_adjoint128_central_fd():
         ad.append(grad[k, j, i])
     fd, ad = np.array(fd), np.array(ad)
     assert np.max(np.abs(fd - ad)) <= 1e-3 * np.max(np.abs(fd))
+
+
+def test_autograd_function():
+    import torch
+    from paper_1705_08019_gb300.autograd import probe_energy
+    w = small_case(dims=(16, 12, 10), nsteps=100)
+    dt = w.cfl_fraction * oracle.cfl_dt(w.dims, w.spacing, w.eps_r)
+    eps = torch.from_numpy(w.eps_r).cuda().requires_grad_(True)
+    sig = torch.from_numpy(w.sigma).cuda()
+    J = probe_energy(eps, w.spacing, dt, w.nsteps, w.sources, w.probes, sigma=sig)
+    (3.0 * J).backward()
+    g = fitgb.Grid(w.dims, w.spacing, w.eps_r, None, w.sigma, 32)
+    J_ref, grad_ref = g.adjoint(dt, w.nsteps, w.sources, w.probes)
+    g.close()
+    assert abs(float(J.item()) - J_ref) <= 1e-12 * J_ref
+    assert eps.grad.dtype == torch.float32
+    assert np.allclose(eps.grad.cpu().numpy(), 3.0 * grad_ref, rtol=1e-6, atol=1e-6 * np.abs(grad_ref).max() * 3)
+    # without a gradient request the forward runs the plain leapfrog only
+    with torch.no_grad():
+        J2 = probe_energy(eps.detach(), w.spacing, dt, w.nsteps, w.sources, w.probes, sigma=sig)
+    assert abs(float(J2.item()) - J_ref) <= 1e-9 * J_ref
