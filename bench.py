@@ -181,8 +181,8 @@ class Clocks:
 def traffic_from_profile():
     """Measured DRAM bytes / algorithmic bytes of the step kernel from the
     committed ncu summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "step_kernel_boxes256.txt")
-    src = os.path.join(ROOT, "paper_1705_08019_gb300", "csrc", "step.cu")
+    path = os.path.join(ROOT, "profiles", "step_tma_kernel_boxes256.md")
+    src = os.path.join(ROOT, "paper_1705_08019_gb300", "csrc", "step_tma.cuh")
     if not os.path.exists(path):
         return None
     vals = {}
@@ -191,7 +191,7 @@ def traffic_from_profile():
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if vals.get("step_cu_sha256") != sha:
+    if vals.get("step_tma_cuh_sha256") != sha:
         return None
     try:
         return float(vals["dram_over_algorithmic"])
@@ -283,7 +283,7 @@ def run_ours(args, rank, world, local_rank):
             "frac": (achieved / peak) if achieved else None,
             "traffic": (ratio * alg / launches) if ratio else None,
             "peak_kind": f"{peak_kind} copy bandwidth",
-            "kernel": "step_kernel (fused E/H leapfrog, all active members)",
+            "kernel": "step_tma_kernel (fused E/H leapfrog, TMA ring, all active members)",
             "alg_bytes_per_launch": alg / launches, "avg_launch_us": 1e3 * step_ms / launches,
             "step_kernel_share": step_ms / (ms * args.steps)}
     extras = {}
