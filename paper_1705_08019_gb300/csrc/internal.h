@@ -48,6 +48,7 @@ struct Member {
     void *st[2];            // the two 6-component state blocks (T)
     int blk[2];             // their block indices in the run's state allocation
     long long start;        // absolute step of the member at iteration 0
+    long long end;          // absolute step it stops at (batched launches skip it there)
     long long src_lo;       // sources act for absolute steps in [src_lo, src_hi)
     long long src_hi;
     double *probe;          // probe rows, row = absolute step - probe_base
@@ -81,6 +82,39 @@ struct StepArgs {
     int *err;
 };
 
+// One grid of a batched launch (device table).
+template <typename T>
+struct GridDesc {
+    int nx, ny, nz, pitch;
+    long long ncell;          // pitch*ny*nz
+    int tiles_x, tiles_y, nchunk, kz;
+    const T *ch;              // 3 values or 3 pitched components
+    int muarr;
+    const Member *mem;        // this grid's member table
+    const double *amp;        // this grid's source table
+    long long amp_base;
+    int nsrc, nprb;
+    EdgeRef src[kMaxSrc];
+    EdgeRef prb[kMaxPrb];
+};
+
+// One unit of work of a batched step: a tile column of one member of one grid.
+struct WorkItem {
+    int grid, member, tile, chunk;
+};
+
+// Arguments of one batched launch (all active members of all grids, one step).
+template <typename T>
+struct BatchArgs {
+    const GridDesc<T> *grids;
+    const CUtensorMap *maps;  // 2 per grid (state, coefficients), 64-byte aligned
+    const WorkItem *items;
+    int nitems;               // items of the launch (inactive members are skipped)
+    int it, parity;
+    int *counter;             // work counter of this launch (zero before it)
+    int *err;
+};
+
 struct Tile {
     int tx, ty, kz;
     int kernel;   // 1: shared-memory staging by plain loads, 2: TMA pipeline
@@ -101,6 +135,10 @@ template <typename T>
 cudaError_t launch_step_tma(const StepArgs<T> &a, const TmaMaps &maps, Tile tile, bool lossy, bool mu_array,
                             bool energy, cudaStream_t s);
 bool tma_tile_supported(int tx, int ty, int elem_bytes);
+// batched persistent kernel (FP32): launch over b.nitems items with `ctas` CTAs
+cudaError_t launch_batched_f32(const BatchArgs<float> &b, Tile tile, bool lossy, int ctas, cudaStream_t s);
+int batched_ctas_per_sm_f32(Tile tile, bool lossy);
+bool batched_tile_supported(int tx, int ty);
 // Encode the two tensor maps of a run; returns false if the driver lacks TMA.
 bool encode_tma_maps(TmaMaps *out, int elem_bytes, int nx, int ny, int nz, int pitch, void *state,
                      int nblocks, const void *coef, int ncoef, int tx, int ty);

@@ -165,6 +165,7 @@ extern "C" int fit_leapfrog_run_static(int nx, int ny, int nz, double dx, double
     m.blk[0] = 0;
     m.blk[1] = 1;
     m.start = step0;
+    m.end = (1LL << 62);
     m.src_lo = -(1LL << 62);
     m.src_hi = (1LL << 62);
     m.probe = (probe_out && nprb > 0) ? probe_out : nullptr;

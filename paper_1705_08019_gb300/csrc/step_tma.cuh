@@ -131,111 +131,127 @@ struct Geometry {
     static constexpr int DYN_SMEM = S * STAGE + 128;   // + room to align the base to 128 B
 };
 
+// Everything one CTA needs to advance one tile column (i0, j0, z chunk) of
+// one member of one grid by one step.
+template <typename T>
+struct TileJob {
+    int nx, ny, nz, pitch;
+    long long ncell;          // pitch*ny*nz
+    int i0, j0, k0, k1;
+    const T *ch;              // 3 values, or 3 pitched components (muarr)
+    const T *meps, *mmu;      // energy only
+    int muarr, energy;
+    long long step;           // absolute step of the member
+    int blk_in;               // state block read (TMA coordinate)
+    T *out;                   // state block written
+    bool src_on;              // sources active at this step
+    const double *amp;
+    long long amp_base;
+    int nsrc;
+    const EdgeRef *src;       // generic pointer (parameter or global space)
+    int nprb;
+    const EdgeRef *prb;
+    double *probe;
+    long long probe_base;
+    double *energy_out;       // energy row of this step, or null
+    int *err;
+};
+
+// Shared memory of the tile pipeline (dynamic stage ring + these statics).
+template <typename T, int TX, int TY, int S>
+struct TileSmem {
+    uint64_t bar[S];
+    T sH[3][TY + 1][TX + 1];   // h^{n+1/2} of plane k with low halos
+    EdgeRef src_ref[kMaxSrc], prb_ref[kMaxPrb];
+    int src_idx[kMaxSrc], prb_idx[kMaxPrb];
+    int nsrc, nprb;
+    double red[TX * TY / 32];
+};
+
+// One tile column of one step.  `phase` holds the parity of each stage's
+// mbarrier; it carries over between calls on the same CTA.  Returns false if
+// a bounded wait gave up (kErrTimeout recorded, no copy left in flight).
 template <typename T, int TX, int TY, int S, bool LOSSY>
-__global__ void __launch_bounds__(TX *TY) step_tma_kernel(const StepArgs<T> a, const __grid_constant__ CUtensorMap tm_state,
-                                                          const __grid_constant__ CUtensorMap tm_coef, int muarr,
-                                                          int energy) {
+__device__ __forceinline__ bool tma_tile(const TileJob<T> &J, const CUtensorMap *tm_state,
+                                         const CUtensorMap *tm_coef, unsigned char *dsm,
+                                         TileSmem<T, TX, TY, S> &sm, uint32_t &phase) {
     using G = Geometry<T, TX, TY, S, LOSSY>;
     constexpr int NT = G::NT, BX = G::BX, EY = G::EY;
     static_assert(S >= 3, "the e plane k+1 is read while plane k+S is in flight");
     static_assert(TX + TY <= NT, "halo threads");
-    extern __shared__ __align__(128) unsigned char dsm_raw[];
-    unsigned char *dsm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(dsm_raw) + 127) &
-                                                           ~static_cast<uintptr_t>(127));
-    __shared__ __align__(8) uint64_t bar[S];
-    __shared__ T sH[3][TY + 1][TX + 1];   // h^{n+1/2} of plane k with low halos
-    __shared__ EdgeRef sSrcRef[kMaxSrc], sPrbRef[kMaxPrb];
-    __shared__ int sSrc[kMaxSrc], sPrb[kMaxPrb];
-    __shared__ int sNsrc, sNprb;
-    __shared__ double sRed[NT / 32];
-
     const int tid = threadIdx.x;
     const int lx = tid % TX, ly = tid / TX;
-
-    int rest = blockIdx.x;   // CTA -> (member, tile, z chunk), member fastest
-    const int m = rest % a.nmem;
-    rest /= a.nmem;
-    const int tile_x = rest % a.tiles_x;
-    rest /= a.tiles_x;
-    const int tile_y = rest % a.tiles_y;
-    const int chunk = rest / a.tiles_y;
-
-    const int nx = a.nx, ny = a.ny, nz = a.nz, pitch = a.pitch;
-    const long long ncell = a.ncell;
-    const int i0 = tile_x * TX, j0 = tile_y * TY;
+    const int nx = J.nx, ny = J.ny, pitch = J.pitch;
+    const long long ncell = J.ncell;
+    const int i0 = J.i0, j0 = J.j0, k0 = J.k0, k1 = J.k1;
     const int i = i0 + lx, j = j0 + ly;
     const bool own = (i < nx) && (j < ny);
-    const int k0 = chunk * a.kz;
-    const int k1 = min(nz, k0 + a.kz);
     const int kstart = (k0 > 0) ? k0 - 1 : k0;   // k0-1: prologue plane (h only)
     const int total = k1 - kstart + 1;            // planes kstart .. k1
-
-    const Member mb = a.mem[m];
-    const long long step = mb.start + a.it;
-    const int blk_in = a.parity ? mb.blk[1] : mb.blk[0];
-    T *__restrict__ out = static_cast<T *>(a.parity ? mb.st[0] : mb.st[1]);
+    T *__restrict__ out = J.out;
 
     if (tid == 0) {
-        for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
-        mbar_init_fence();
         int ns = 0, np = 0;
-        const bool on = step >= mb.src_lo && step < mb.src_hi;
-#pragma unroll
-        for (int s = 0; s < kMaxSrc; ++s) {
-            const EdgeRef r = a.src[s];
-            if (on && s < a.nsrc && r.i >= i0 && r.i < i0 + TX && r.j >= j0 && r.j < j0 + TY && r.k >= k0 &&
-                r.k < k1) {
-                sSrc[ns] = s;
-                sSrcRef[ns] = r;
+        for (int s = 0; s < J.nsrc && J.src_on; ++s) {
+            const EdgeRef r = J.src[s];
+            if (r.i >= i0 && r.i < i0 + TX && r.j >= j0 && r.j < j0 + TY && r.k >= k0 && r.k < k1) {
+                sm.src_idx[ns] = s;
+                sm.src_ref[ns] = r;
                 ++ns;
             }
         }
-#pragma unroll
-        for (int p = 0; p < kMaxPrb; ++p) {
-            const EdgeRef r = a.prb[p];
-            if (mb.probe && p < a.nprb && r.i >= i0 && r.i < i0 + TX && r.j >= j0 && r.j < j0 + TY &&
-                r.k >= k0 && r.k < k1) {
-                sPrb[np] = p;
-                sPrbRef[np] = r;
+        for (int p = 0; p < J.nprb && J.probe; ++p) {
+            const EdgeRef r = J.prb[p];
+            if (r.i >= i0 && r.i < i0 + TX && r.j >= j0 && r.j < j0 + TY && r.k >= k0 && r.k < k1) {
+                sm.prb_idx[np] = p;
+                sm.prb_ref[np] = r;
                 ++np;
             }
         }
-        sNsrc = ns;
-        sNprb = np;
+        sm.nsrc = ns;
+        sm.nprb = np;
     }
     __syncthreads();
 
     auto issue = [&](int p) {   // thread 0: start the copies of plane kstart + p
         const int kk = kstart + p;
         unsigned char *st = dsm + (p % S) * G::STAGE;
-        uint64_t *b = &bar[p % S];
+        uint64_t *b = &sm.bar[p % S];
         mbar_expect_tx(b, G::TX_BYTES);
-        tma_load_5d(st, &tm_state, b, i0 - 4, j0 - 1, kk, 0, blk_in);
-        tma_load_5d(st + G::H_OFF, &tm_state, b, i0 - 4, j0 - 1, kk, 3, blk_in);
-        tma_load_4d(st + G::C_OFF, &tm_coef, b, i0, j0, kk, 0);
+        tma_load_5d(st, tm_state, b, i0 - 4, j0 - 1, kk, 0, J.blk_in);
+        tma_load_5d(st + G::H_OFF, tm_state, b, i0 - 4, j0 - 1, kk, 3, J.blk_in);
+        tma_load_4d(st + G::C_OFF, tm_coef, b, i0, j0, kk, 0);
+    };
+    // wait for plane p (its stage's parity flips with every use)
+    auto wait_plane = [&](int p) -> bool {
+        const int st = p % S;
+        const bool ok = mbar_wait(&sm.bar[st], (phase >> st) & 1u);
+        if (ok) phase ^= (1u << st);
+        return ok;
     };
     int issued = 0;
     if (tid == 0) {
+        proxy_fence();
         for (; issued < min(S, total); ++issued) issue(issued);
     }
 
     T ch[3] = {T(0), T(0), T(0)};
-    if (!muarr) {
-        ch[0] = a.ch[0];
-        ch[1] = a.ch[1];
-        ch[2] = a.ch[2];
+    if (!J.muarr) {
+        ch[0] = J.ch[0];
+        ch[1] = J.ch[1];
+        ch[2] = J.ch[2];
     }
     T mmu_c[3] = {T(0), T(0), T(0)};
-    if (energy && !muarr) {
-        mmu_c[0] = a.mmu[0];
-        mmu_c[1] = a.mmu[1];
-        mmu_c[2] = a.mmu[2];
+    if (J.energy && !J.muarr) {
+        mmu_c[0] = J.mmu[0];
+        mmu_c[1] = J.mmu[1];
+        mmu_c[2] = J.mmu[2];
     }
-    const bool hx_col = tid < TY;                  // low-x halo column
+    const bool hx_col = tid < TY;                   // low-x halo column
     const bool hy_row = tid >= TY && tid < TY + TX; // low-y halo row
     T hxp = T(0), hyp = T(0);   // h_x, h_y at (i, j, k-1), step n+1/2
     Acc<T> wacc;
-    int bad = mbar_wait(&bar[0], 0) ? 0 : 1;
+    int bad = wait_plane(0) ? 0 : 1;
     int waited = bad ? 0 : 1;   // planes whose copies are known complete
     bool aborted = false;
 
@@ -247,17 +263,17 @@ __global__ void __launch_bounds__(TX *TY) step_tma_kernel(const StepArgs<T> a, c
         const T *cC = reinterpret_cast<const T *>(dsm + (p % S) * G::STAGE + G::C_OFF);
         const T *eN = reinterpret_cast<const T *>(dsm + ((p + 1) % S) * G::STAGE);
         if (!bad) {
-            if (mbar_wait(&bar[(p + 1) % S], ((p + 1) / S) & 1)) waited = p + 2;
+            if (wait_plane(p + 1)) waited = p + 2;
             else bad = 1;
         }
 #define EV(buf, comp, y, x) (buf)[((comp) * EY + (y)) * BX + (x)]
         const int sx = lx + 4, sy = ly + 1;
         const long long c = ((long long)k * ny + j) * pitch + i;
         T chl0 = ch[0], chl1 = ch[1], chl2 = ch[2];
-        if (muarr) {
-            chl0 = own ? a.ch[c] : T(0);
-            chl1 = own ? a.ch[ncell + c] : T(0);
-            chl2 = own ? a.ch[2 * ncell + c] : T(0);
+        if (J.muarr) {
+            chl0 = own ? J.ch[c] : T(0);
+            chl1 = own ? J.ch[ncell + c] : T(0);
+            chl2 = own ? J.ch[2 * ncell + c] : T(0);
         }
         const T ex0 = EV(eC, 0, sy, sx), ey0 = EV(eC, 1, sy, sx), ez0 = EV(eC, 2, sy, sx);
         const T ho0 = EV(hC, 0, sy, sx), ho1 = EV(hC, 1, sy, sx), ho2 = EV(hC, 2, sy, sx);
@@ -271,37 +287,37 @@ __global__ void __launch_bounds__(TX *TY) step_tma_kernel(const StepArgs<T> a, c
         const T hyn = ho1 - chl1 * cy;
         const T hzn = ho2 - chl2 * cz;
         if (!pro) {
-            sH[0][sy][lx + 1] = hxn;
-            sH[1][sy][lx + 1] = hyn;
-            sH[2][sy][lx + 1] = hzn;
+            sm.sH[0][sy][lx + 1] = hxn;
+            sm.sH[1][sy][lx + 1] = hyn;
+            sm.sH[2][sy][lx + 1] = hzn;
             if (hx_col) {   // cell (i0-1, j0+tid): window x = 3
                 const int y = tid + 1;
                 T c1 = ch[1], c2 = ch[2];
-                if (muarr) {
+                if (J.muarr) {
                     const int hi = i0 - 1, hj = j0 + tid;
                     const bool in = hi >= 0 && hj < ny;
                     const long long hc = ((long long)k * ny + hj) * pitch + hi;
-                    c1 = in ? a.ch[ncell + hc] : T(0);
-                    c2 = in ? a.ch[2 * ncell + hc] : T(0);
+                    c1 = in ? J.ch[ncell + hc] : T(0);
+                    c2 = in ? J.ch[2 * ncell + hc] : T(0);
                 }
                 const T cyh = EV(eC, 2, y, 3) + EV(eN, 0, y, 3) - EV(eC, 2, y, 4) - EV(eC, 0, y, 3);
                 const T czh = EV(eC, 0, y, 3) + EV(eC, 1, y, 4) - EV(eC, 0, y + 1, 3) - EV(eC, 1, y, 3);
-                sH[1][y][0] = EV(hC, 1, y, 3) - c1 * cyh;
-                sH[2][y][0] = EV(hC, 2, y, 3) - c2 * czh;
+                sm.sH[1][y][0] = EV(hC, 1, y, 3) - c1 * cyh;
+                sm.sH[2][y][0] = EV(hC, 2, y, 3) - c2 * czh;
             } else if (hy_row) {   // cell (i0+t, j0-1): window y = 0
                 const int t = tid - TY, x = t + 4;
                 T c0 = ch[0], c2 = ch[2];
-                if (muarr) {
+                if (J.muarr) {
                     const int hi = i0 + t, hj = j0 - 1;
                     const bool in = hj >= 0 && hi < nx;
                     const long long hc = ((long long)k * ny + hj) * pitch + hi;
-                    c0 = in ? a.ch[hc] : T(0);
-                    c2 = in ? a.ch[2 * ncell + hc] : T(0);
+                    c0 = in ? J.ch[hc] : T(0);
+                    c2 = in ? J.ch[2 * ncell + hc] : T(0);
                 }
                 const T cxh = EV(eC, 1, 0, x) + EV(eC, 2, 1, x) - EV(eN, 1, 0, x) - EV(eC, 2, 0, x);
                 const T czh = EV(eC, 0, 0, x) + EV(eC, 1, 0, x + 1) - EV(eC, 0, 1, x) - EV(eC, 1, 0, x);
-                sH[0][0][t + 1] = EV(hC, 0, 0, x) - c0 * cxh;
-                sH[2][0][t + 1] = EV(hC, 2, 0, x) - c2 * czh;
+                sm.sH[0][0][t + 1] = EV(hC, 0, 0, x) - c0 * cxh;
+                sm.sH[2][0][t + 1] = EV(hC, 2, 0, x) - c2 * czh;
             }
             if (own) {
                 out[3 * ncell + c] = hxn;
@@ -317,15 +333,15 @@ __global__ void __launch_bounds__(TX *TY) step_tma_kernel(const StepArgs<T> a, c
         if (!pro && own) {
             const int sxh = lx + 1;
             // (C~h)_x = h_z(q) - h_z(q-y) - h_y(q) + h_y(q-z)
-            T tx = hzn - sH[2][sy - 1][sxh] - hyn + hyp;
+            T tx = hzn - sm.sH[2][sy - 1][sxh] - hyn + hyp;
             // (C~h)_y = h_x(q) - h_x(q-z) - h_z(q) + h_z(q-x)
-            T ty = hxn - hxp - hzn + sH[2][sy][sxh - 1];
+            T ty = hxn - hxp - hzn + sm.sH[2][sy][sxh - 1];
             // (C~h)_z = h_y(q) - h_y(q-x) - h_x(q) + h_x(q-y)
-            T tz = hyn - sH[1][sy][sxh - 1] - hxn + sH[0][sy - 1][sxh];
-            for (int q = 0; q < sNsrc; ++q) {
-                const EdgeRef r = sSrcRef[q];
+            T tz = hyn - sm.sH[1][sy][sxh - 1] - hxn + sm.sH[0][sy - 1][sxh];
+            for (int q = 0; q < sm.nsrc; ++q) {
+                const EdgeRef r = sm.src_ref[q];
                 if (r.i == i && r.j == j && r.k == k) {
-                    const T jv = (T)a.amp[(step - a.amp_base) * a.nsrc + sSrc[q]];
+                    const T jv = (T)J.amp[(J.step - J.amp_base) * J.nsrc + sm.src_idx[q]];
                     if (r.axis == 0) tx -= jv;
                     else if (r.axis == 1) ty -= jv;
                     else tz -= jv;
@@ -346,20 +362,20 @@ __global__ void __launch_bounds__(TX *TY) step_tma_kernel(const StepArgs<T> a, c
             out[c] = exn;
             out[ncell + c] = eyn;
             out[2 * ncell + c] = ezn;
-            for (int q = 0; q < sNprb; ++q) {
-                const EdgeRef r = sPrbRef[q];
+            for (int q = 0; q < sm.nprb; ++q) {
+                const EdgeRef r = sm.prb_ref[q];
                 if (r.i == i && r.j == j && r.k == k) {
                     const T v = r.axis == 0 ? exn : (r.axis == 1 ? eyn : ezn);
-                    mb.probe[(step - mb.probe_base) * a.nprb + sPrb[q]] = (double)v;
+                    J.probe[(J.step - J.probe_base) * J.nprb + sm.prb_idx[q]] = (double)v;
                 }
             }
-            if (energy) {
-                const T me0 = a.meps[c], me1 = a.meps[ncell + c], me2 = a.meps[2 * ncell + c];
+            if (J.energy) {
+                const T me0 = J.meps[c], me1 = J.meps[ncell + c], me2 = J.meps[2 * ncell + c];
                 T mu0 = mmu_c[0], mu1 = mmu_c[1], mu2 = mmu_c[2];
-                if (muarr) {
-                    mu0 = a.mmu[c];
-                    mu1 = a.mmu[ncell + c];
-                    mu2 = a.mmu[2 * ncell + c];
+                if (J.muarr) {
+                    mu0 = J.mmu[c];
+                    mu1 = J.mmu[ncell + c];
+                    mu2 = J.mmu[2 * ncell + c];
                 }
                 wacc.add(me0 * ex0 * ex0);
                 wacc.add(me1 * ey0 * ey0);
@@ -381,22 +397,119 @@ __global__ void __launch_bounds__(TX *TY) step_tma_kernel(const StepArgs<T> a, c
 
     if (aborted) {
         if (tid == 0) {
-            atomicOr(a.err, kErrTimeout);
+            atomicOr(J.err, kErrTimeout);
             // do not leave while copies into this CTA's shared memory are pending
-            for (int p = waited; p < issued; ++p) mbar_wait(&bar[p % S], (p / S) & 1);
+            for (int p = waited; p < issued; ++p) wait_plane(p);
         }
-        return;
+        return false;
     }
-    if (energy) {
+    if (J.energy) {
         double v = wacc.value();
         for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-        if ((tid & 31) == 0) sRed[tid >> 5] = v;
+        if ((tid & 31) == 0) sm.red[tid >> 5] = v;
         __syncthreads();
         if (tid == 0) {
             double t = 0.0;
-            for (int w = 0; w < NT / 32; ++w) t += sRed[w];
-            if (mb.energy) atomicAdd(mb.energy + (step - mb.energy_base), t);
+            for (int w = 0; w < NT / 32; ++w) t += sm.red[w];
+            if (J.energy_out) atomicAdd(J.energy_out, t);
         }
+        __syncthreads();
+    }
+    return true;
+}
+
+template <typename T, int TX, int TY, int S>
+__device__ __forceinline__ unsigned char *aligned_dsm() {
+    extern __shared__ __align__(128) unsigned char dsm_raw[];
+    return reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(dsm_raw) + 127) &
+                                             ~static_cast<uintptr_t>(127));
+}
+
+// Single grid: one CTA = one (member, tile, chunk), member fastest.
+template <typename T, int TX, int TY, int S, bool LOSSY>
+__global__ void __launch_bounds__(TX *TY) step_tma_kernel(const __grid_constant__ StepArgs<T> a,
+                                                          const __grid_constant__ CUtensorMap tm_state,
+                                                          const __grid_constant__ CUtensorMap tm_coef, int muarr,
+                                                          int energy) {
+    __shared__ TileSmem<T, TX, TY, S> sm;
+    unsigned char *dsm = aligned_dsm<T, TX, TY, S>();
+    int rest = blockIdx.x;
+    const int m = rest % a.nmem;
+    rest /= a.nmem;
+    const int tile_x = rest % a.tiles_x;
+    rest /= a.tiles_x;
+    const int tile_y = rest % a.tiles_y;
+    const int chunk = rest / a.tiles_y;
+    const Member mb = a.mem[m];
+    TileJob<T> J;
+    J.nx = a.nx; J.ny = a.ny; J.nz = a.nz; J.pitch = a.pitch; J.ncell = a.ncell;
+    J.i0 = tile_x * TX;
+    J.j0 = tile_y * TY;
+    J.k0 = chunk * a.kz;
+    J.k1 = min(a.nz, J.k0 + a.kz);
+    J.ch = a.ch; J.meps = a.meps; J.mmu = a.mmu; J.muarr = muarr; J.energy = energy;
+    J.step = mb.start + a.it;
+    J.blk_in = a.parity ? mb.blk[1] : mb.blk[0];
+    J.out = static_cast<T *>(a.parity ? mb.st[0] : mb.st[1]);
+    J.src_on = J.step >= mb.src_lo && J.step < mb.src_hi;
+    J.amp = a.amp; J.amp_base = a.amp_base; J.nsrc = a.nsrc; J.src = a.src;
+    J.nprb = a.nprb; J.prb = a.prb; J.probe = mb.probe; J.probe_base = mb.probe_base;
+    J.energy_out = (energy && mb.energy) ? mb.energy + (J.step - mb.energy_base) : nullptr;
+    J.err = a.err;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&sm.bar[s], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    tma_tile<T, TX, TY, S, LOSSY>(J, &tm_state, &tm_coef, dsm, sm, phase);
+}
+
+// Many grids: persistent CTAs (about one per resident slot) take work items
+// from an atomic counter until the list is exhausted.  Items are ordered by
+// (grid, tile, chunk, member), members innermost, so the CTAs working on one
+// tile of different members run side by side and share its coefficients in
+// L2; a member past its last step is skipped.
+template <typename T, int TX, int TY, int S, bool LOSSY>
+__global__ void __launch_bounds__(TX *TY) batched_tma_kernel(const __grid_constant__ BatchArgs<T> b) {
+    __shared__ TileSmem<T, TX, TY, S> sm;
+    unsigned char *dsm = aligned_dsm<T, TX, TY, S>();
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&sm.bar[s], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(b.counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= b.nitems) break;
+        const WorkItem w = b.items[item];
+        const GridDesc<T> &gd = b.grids[w.grid];
+        const Member mb = gd.mem[w.member];
+        if (mb.start + b.it >= mb.end) continue;   // member finished: nothing to do
+        const int tile_x = w.tile % gd.tiles_x;
+        const int tile_y = w.tile / gd.tiles_x;
+        TileJob<T> J;
+        J.nx = gd.nx; J.ny = gd.ny; J.nz = gd.nz; J.pitch = gd.pitch; J.ncell = gd.ncell;
+        J.i0 = tile_x * TX;
+        J.j0 = tile_y * TY;
+        J.k0 = w.chunk * gd.kz;
+        J.k1 = min(gd.nz, J.k0 + gd.kz);
+        J.ch = gd.ch; J.meps = nullptr; J.mmu = nullptr; J.muarr = gd.muarr; J.energy = 0;
+        J.step = mb.start + b.it;
+        J.blk_in = b.parity ? mb.blk[1] : mb.blk[0];
+        J.out = static_cast<T *>(b.parity ? mb.st[0] : mb.st[1]);
+        J.src_on = J.step >= mb.src_lo && J.step < mb.src_hi;
+        J.amp = gd.amp; J.amp_base = gd.amp_base; J.nsrc = gd.nsrc; J.src = gd.src;
+        J.nprb = gd.nprb; J.prb = gd.prb; J.probe = mb.probe; J.probe_base = mb.probe_base;
+        J.energy_out = nullptr;
+        J.err = b.err;
+        if (!tma_tile<T, TX, TY, S, LOSSY>(J, &b.maps[2 * w.grid], &b.maps[2 * w.grid + 1], dsm, sm, phase))
+            return;
     }
 }
 
@@ -416,6 +529,37 @@ cudaError_t launch_one(const StepArgs<T> &a, const TmaMaps &maps, bool muarr, bo
     step_tma_kernel<T, TX, TY, S, LOSSY><<<(unsigned)blocks, TX * TY, G::DYN_SMEM, s>>>(
         a, maps.state, maps.coef, muarr ? 1 : 0, energy ? 1 : 0);
     return cudaGetLastError();
+}
+
+template <typename T, int TX, int TY, int S, bool LOSSY>
+cudaError_t launch_batched_one(const BatchArgs<T> &b, int ctas, cudaStream_t s) {
+    using G = Geometry<T, TX, TY, S, LOSSY>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(batched_tma_kernel<T, TX, TY, S, LOSSY>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, G::DYN_SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (b.nitems <= 0) return cudaSuccess;
+    const int grid = ctas < b.nitems ? ctas : b.nitems;
+    batched_tma_kernel<T, TX, TY, S, LOSSY><<<grid, TX * TY, G::DYN_SMEM, s>>>(b);
+    return cudaGetLastError();
+}
+
+// resident CTAs per SM of a batched configuration (for the persistent grid size)
+template <typename T, int TX, int TY, int S, bool LOSSY>
+int batched_occupancy() {
+    using G = Geometry<T, TX, TY, S, LOSSY>;
+    int n = 0;
+    cudaFuncSetAttribute(batched_tma_kernel<T, TX, TY, S, LOSSY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         G::DYN_SMEM);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batched_tma_kernel<T, TX, TY, S, LOSSY>, TX * TY,
+                                                      G::DYN_SMEM) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n > 0 ? n : 1;
 }
 
 }  // namespace tma

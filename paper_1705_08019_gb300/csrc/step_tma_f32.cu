@@ -27,6 +27,37 @@ cudaError_t launch_step_tma<float>(const StepArgs<float> &a, const TmaMaps &maps
     return cudaErrorInvalidValue;
 }
 
+bool batched_tile_supported(int tx, int ty) {
+    return (tx == 32 && (ty == 4 || ty == 8 || ty == 16)) || (tx == 64 && ty == 4);
+}
+
+cudaError_t launch_batched_f32(const BatchArgs<float> &b, Tile t, bool lossy, int ctas, cudaStream_t s) {
+    using namespace tma;
+#define FIT_T(TX, TY, S)                                                                          \
+    if (t.tx == TX && t.ty == TY)                                                                 \
+        return lossy ? launch_batched_one<float, TX, TY, S, true>(b, ctas, s)                     \
+                     : launch_batched_one<float, TX, TY, S, false>(b, ctas, s);
+    FIT_T(32, 8, 4)
+    FIT_T(32, 16, 3)
+    FIT_T(32, 4, 4)
+    FIT_T(64, 4, 4)
+#undef FIT_T
+    return cudaErrorInvalidValue;
+}
+
+int batched_ctas_per_sm_f32(Tile t, bool lossy) {
+    using namespace tma;
+#define FIT_T(TX, TY, S)                                                                          \
+    if (t.tx == TX && t.ty == TY)                                                                 \
+        return lossy ? batched_occupancy<float, TX, TY, S, true>() : batched_occupancy<float, TX, TY, S, false>();
+    FIT_T(32, 8, 4)
+    FIT_T(32, 16, 3)
+    FIT_T(32, 4, 4)
+    FIT_T(64, 4, 4)
+#undef FIT_T
+    return 1;
+}
+
 namespace {
 PFN_cuTensorMapEncodeTiled_v12000 encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
