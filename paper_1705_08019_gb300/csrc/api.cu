@@ -1038,8 +1038,6 @@ int batched_group(const std::vector<const fit_paraexp_problem *> &probs, bool lo
             host_out = host_out || !is_device(q.h_final);
         }
         g->stats.kernel_launches = g->stats.step_launches;   // shared launches, counted per grid
-        g->tile = tile;
-        g->tile.kernel = 2;
     }
     // temporary tables are freed when this call returns: wait for the work
     FIT_CHECK(cudaStreamSynchronize(s));
