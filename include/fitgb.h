@@ -30,8 +30,9 @@
  *   and are not stored.  Entries that are not degrees of freedom (e
  *   tangential to a wall, h normal to a wall) are ignored on input and
  *   returned as zero.
- * Precision: a grid is created for FP32 or FP64 fields; field arrays passed
- *   to it (e_io, h_io) are float or double accordingly.  Probe traces,
+ * Precision: a grid is created for FP32, FP64 or compensated-FP32 fields;
+ *   field arrays passed to it (e_io, h_io) are float for FP32 and double
+ *   otherwise.  Probe traces,
  *   energies, superposed fields, J and gradients are always double.
  * Pointers: every array argument may be a host or a device pointer; the
  *   library finds out with cudaPointerGetAttributes.  The caller owns all
@@ -121,7 +122,13 @@ typedef struct {
 
 /* Create a grid and upload its per-cell materials.
  *   eps_r (required), mu_r (NULL = 1), sigma [S/m] (NULL = 0): nx*ny*nz.
- *   precision: 32 (float fields) or 64 (double fields).
+ *   precision: 32 (float fields), 64 (double fields), or 48: compensated
+ *     FP32 fields, each value an unevaluated sum hi + lo of two floats (about
+ *     48 significant bits), advanced in FP32 arithmetic with error-free sums
+ *     and products; its field arrays (e_io, h_io, e0, h0) are double.
+ *     The compensated mode runs fit_leapfrog_run and paraexp_run (FP64
+ *     superposition) with the TMA kernel; fit_adjoint_grad returns
+ *     FIT_ERR_UNSUPPORTED for it.
  * Material matrices (Sec. II, eq. maxwell_grid3): M_eps on an edge is eps0
  * times the area-weighted mean of eps_r over the four cells around it, times
  * dual area / length; M_sigma likewise; M_mu on a face is mu0 times the

@@ -173,7 +173,12 @@ Tile pick_tile(const fit_grid *g, const fit_run_opts *o) {
         t.tx = o->tile_x;
         t.ty = o->tile_y;
     }
-    if (t.kernel == 2 && !tma_tile_supported(t.tx, t.ty, g->prec == 64 ? 8 : 4)) t.kernel = 1;
+    if (g->prec == 48) {
+        if (!comp_tile_supported(t.tx, t.ty)) t.tx = 32, t.ty = 8;
+        t.kernel = 2;
+    } else if (t.kernel == 2 && !tma_tile_supported(t.tx, t.ty, g->prec == 64 ? 8 : 4)) {
+        t.kernel = 1;
+    }
     if (t.kernel == 1 && !tile_supported(t.tx, t.ty)) {
         t.tx = 32;
         t.ty = 8;
@@ -199,7 +204,8 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
                 const fit_run_opts *opts, cudaStream_t s) {
     const long long ncell = g->ncell;   // real cells (algorithmic counts)
     const long long ncp = g->ncp;       // padded component stride (device arrays)
-    const size_t n6 = 6 * (size_t)ncp;
+    const bool comp = g->prec == 48;    // hi/lo float pairs: 12-component state blocks
+    const size_t n6 = (comp ? 12 : 6) * (size_t)ncp;
     const size_t row = (size_t)g->nx * sizeof(T), prow = (size_t)g->pitch * sizeof(T);
     const size_t rows3 = 3 * (size_t)g->ny * g->nz;
     int rc;
@@ -210,7 +216,7 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
     long long nev = 0;   // events recorded (pairs around step launches)
     // algorithmic bytes of one step launch: fields of every member once in and
     // once out, plus the coefficient arrays once
-    const double fld_bytes = 12.0 * sizeof(T) * (double)ncell;
+    const double fld_bytes = (comp ? 24.0 : 12.0) * sizeof(T) * (double)ncell;
     const double coef_bytes = ((g->lossy ? 6.0 : 3.0) + (g->mu_array ? 3.0 : 0.0) +
                                (energy_dev ? (3.0 + (g->mu_array ? 3.0 : 0.0)) : 0.0)) * sizeof(T) * (double)ncell;
 
@@ -238,7 +244,7 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
     FIT_CHECK(cudaMemsetAsync(g->err.p, 0, sizeof(int), s));
     if (probes) FIT_CHECK(cudaMemsetAsync(g->pm.p, 0, sizeof(double) * (size_t)probe_rows * nprb * nm_total, s));
     if (energy_dev) FIT_CHECK(cudaMemsetAsync(energy_dev, 0, sizeof(double) * (size_t)specs_in[0].nit, s));
-    const bool kahan = sum_mode == 1 && acc_e;
+    const bool kahan = sum_mode == 1 && acc_e && !comp;
     if (kahan) {
         if ((rc = ensure(g->kahan, 2 * n6 * sizeof(float)))) return rc;
         FIT_CHECK(cudaMemsetAsync(g->kahan.p, 0, 2 * n6 * sizeof(float), s));
@@ -269,12 +275,42 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
     for (int q = 0; q < nprb; ++q) a.prb[q] = {prb[q].axis, prb[q].i, prb[q].j, prb[q].k};
     a.err = (int *)g->err.p;
     TmaMaps maps;
-    if (tile.kernel == 2 &&
-        !encode_tma_maps(&maps, (int)sizeof(T), g->nx, g->ny, g->nz, g->pitch, g->state.p, 2 * mpp, g->coef.p,
-                         g->lossy ? 6 : 3, tile.tx, tile.ty)) {
+    if (comp) {
+        if (!comp_tile_supported(tile.tx, tile.ty)) tile.tx = 32, tile.ty = 8;
+        if (!encode_tma_maps(&maps, (int)sizeof(T), g->nx, g->ny, g->nz, g->pitch, g->state.p, 2 * mpp, g->coef.p,
+                             g->lossy ? 6 : 3, tile.tx, tile.ty, 12))
+            return FIT_ERR_UNSUPPORTED;
+    } else if (tile.kernel == 2 &&
+               !encode_tma_maps(&maps, (int)sizeof(T), g->nx, g->ny, g->nz, g->pitch, g->state.p, 2 * mpp,
+                                g->coef.p, g->lossy ? 6 : 3, tile.tx, tile.ty)) {
         tile.kernel = 1;
         if (!tile_supported(tile.tx, tile.ty)) tile.tx = 32, tile.ty = 8;
     }
+
+    // member 0's final state -> (final_e, final_h): compact rows of T, or FP64
+    // joined from the hi/lo pairs of a compensated grid
+    auto copy_out = [&](const T *fin) -> int {
+        for (int part = 0; part < 2; ++part) {
+            void *dst = part ? final_h : final_e;
+            if (!dst) continue;
+            if (!comp) {
+                FIT_CHECK(cudaMemcpy2DAsync(dst, row, fin + 3 * part * ncp, prow, row, rows3, kind_from_dev(dst), s));
+                continue;
+            }
+            double *dout = (double *)dst;
+            const bool host = !is_device(dst);
+            if (host) {
+                int r2;
+                if ((r2 = ensure(g->stage, 3 * (size_t)ncell * sizeof(double)))) return r2;
+                dout = (double *)g->stage.p;
+            }
+            FIT_CHECK(join_pairs(g->nx, g->ny, g->nz, g->pitch, (const float *)(fin + 3 * part * ncp),
+                                 (const float *)(fin + (6 + 3 * part) * ncp), dout, s));
+            if (host)
+                FIT_CHECK(cudaMemcpyAsync(dst, dout, 3 * (size_t)ncell * sizeof(double), cudaMemcpyDeviceToHost, s));
+        }
+        return FIT_OK;
+    };
 
     // Groups run from the end of the table (shortest members) to its start, and
     // inside a group members finish shortest first, so the superposition adds
@@ -300,11 +336,28 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
             mem[q].energy_base = sp.start;
             // initial state into buffer 0
             FIT_CHECK(cudaMemsetAsync(base, 0, n6 * sizeof(T), s));
-            if (sp.e0)
-                FIT_CHECK(cudaMemcpy2DAsync(base, prow, sp.e0, row, row, rows3, kind_to_dev(sp.e0), s));
-            if (sp.h0)
-                FIT_CHECK(cudaMemcpy2DAsync(base + 3 * ncp, prow, sp.h0, row, row, rows3, kind_to_dev(sp.h0), s));
-            if (sp.e0 || sp.h0) {
+            if (comp) {   // FP64 compact input -> hi/lo pairs (masked to the degrees of freedom)
+                for (int part = 0; part < 2; ++part) {
+                    const void *src0 = part ? sp.h0 : sp.e0;
+                    if (!src0) continue;
+                    const double *din = (const double *)src0;
+                    if (!is_device(src0)) {
+                        if ((rc = ensure(g->stage, 3 * (size_t)ncell * sizeof(double)))) return rc;
+                        FIT_CHECK(cudaMemcpyAsync(g->stage.p, src0, 3 * (size_t)ncell * sizeof(double),
+                                                  cudaMemcpyHostToDevice, s));
+                        din = (const double *)g->stage.p;
+                    }
+                    FIT_CHECK(split_pairs(g->nx, g->ny, g->nz, g->pitch, din, (float *)(base + 3 * part * ncp),
+                                          (float *)(base + (6 + 3 * part) * ncp), part, s));
+                    g->stats.kernel_launches += 1;
+                }
+            } else {
+                if (sp.e0)
+                    FIT_CHECK(cudaMemcpy2DAsync(base, prow, sp.e0, row, row, rows3, kind_to_dev(sp.e0), s));
+                if (sp.h0)
+                    FIT_CHECK(cudaMemcpy2DAsync(base + 3 * ncp, prow, sp.h0, row, row, rows3, kind_to_dev(sp.h0), s));
+            }
+            if (!comp && (sp.e0 || sp.h0)) {
                 FIT_CHECK(mask_state<T>(g->nx, g->ny, g->nz, g->pitch, base, base + 3 * ncp, s));
                 g->stats.kernel_launches += 1;
             }
@@ -328,7 +381,10 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
                 }
                 FIT_CHECK(cudaEventRecord(g->ev[2 * nev], s));
             }
-            if (tile.kernel == 2)
+            if (comp)
+                FIT_CHECK(launch_step_comp((const StepArgs<float> &)a, maps, tile, g->lossy, g->mu_array,
+                                           energy_dev != nullptr, s));
+            else if (tile.kernel == 2)
                 FIT_CHECK(launch_step_tma<T>(a, maps, tile, g->lossy, g->mu_array, energy_dev != nullptr, s));
             else
                 FIT_CHECK(launch_step<T>(a, tile, g->lossy, g->mu_array, energy_dev != nullptr, s));
@@ -350,6 +406,15 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
                         float *ks = (float *)g->kahan.p;
                         FIT_CHECK(accumulate_state_kahan<T>((long long)n6, fin, ks, ks + n6, s));
                         g->stats.kernel_launches += 1;
+                    } else if (comp) {
+                        FIT_CHECK(accumulate_pairs(3 * ncp, (const float *)fin, (const float *)(fin + 6 * ncp),
+                                                   acc_e, s));
+                        g->stats.kernel_launches += 1;
+                        if (acc_h) {
+                            FIT_CHECK(accumulate_pairs(3 * ncp, (const float *)(fin + 3 * ncp),
+                                                       (const float *)(fin + 9 * ncp), acc_h, s));
+                            g->stats.kernel_launches += 1;
+                        }
                     } else {
                         FIT_CHECK(accumulate_state<T>(3 * ncp, fin, acc_e, s));
                         g->stats.kernel_launches += 1;
@@ -359,13 +424,7 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
                         }
                     }
                 }
-                if (order[first + q] == 0) {
-                    if (final_e)
-                        FIT_CHECK(cudaMemcpy2DAsync(final_e, row, fin, prow, row, rows3, kind_from_dev(final_e), s));
-                    if (final_h)
-                        FIT_CHECK(cudaMemcpy2DAsync(final_h, row, fin + 3 * ncp, prow, row, rows3,
-                                                    kind_from_dev(final_h), s));
-                }
+                if (order[first + q] == 0 && (rc = copy_out(fin))) return rc;
             }
         }
         // zero-length members: their final state is the initial one
@@ -373,20 +432,19 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
             const MemberSpec &sp = specs_in[order[first + q]];
             if (sp.nit > 0) continue;
             const T *fin = (const T *)mem[q].st[0];
-            if (acc_e && !kahan) {
+            if (acc_e && comp) {
+                FIT_CHECK(accumulate_pairs(3 * ncp, (const float *)fin, (const float *)(fin + 6 * ncp), acc_e, s));
+                if (acc_h)
+                    FIT_CHECK(accumulate_pairs(3 * ncp, (const float *)(fin + 3 * ncp), (const float *)(fin + 9 * ncp),
+                                               acc_h, s));
+            } else if (acc_e && !kahan) {
                 FIT_CHECK(accumulate_state<T>(3 * ncp, fin, acc_e, s));
                 if (acc_h) FIT_CHECK(accumulate_state<T>(3 * ncp, fin + 3 * ncp, acc_h, s));
             } else if (kahan) {
                 float *ks = (float *)g->kahan.p;
                 FIT_CHECK(accumulate_state_kahan<T>((long long)n6, fin, ks, ks + n6, s));
             }
-            if (order[first + q] == 0) {
-                if (final_e)
-                    FIT_CHECK(cudaMemcpy2DAsync(final_e, row, fin, prow, row, rows3, kind_from_dev(final_e), s));
-                if (final_h)
-                    FIT_CHECK(cudaMemcpy2DAsync(final_h, row, fin + 3 * ncp, prow, row, rows3,
-                                                kind_from_dev(final_h), s));
-            }
+            if (order[first + q] == 0 && (rc = copy_out(fin))) return rc;
         }
     }
     if (kahan) {
@@ -1075,7 +1133,7 @@ int fit_grid_create(int nx, int ny, int nz, double dx, double dy, double dz, con
     if (nx < 1 || ny < 1 || nz < 1 || !eps_r) return FIT_ERR_ARG;
     if (!(dx > 0) || !(dy > 0) || !(dz > 0) || !std::isfinite(dx) || !std::isfinite(dy) || !std::isfinite(dz))
         return FIT_ERR_ARG;
-    if (precision != 32 && precision != 64) return FIT_ERR_ARG;
+    if (precision != 32 && precision != 64 && precision != 48) return FIT_ERR_ARG;
     const long long ncell = (long long)nx * ny * nz;
     if (ncell > (1LL << 34)) return FIT_ERR_ARG;
     fit_grid *g = new (std::nothrow) fit_grid();
@@ -1157,6 +1215,7 @@ int fit_leapfrog_run(fit_grid *g, double dt, long nsteps, long step0, const fit_
     if (g->prec == 64)
         return leapfrog_impl<double>(g, dt, nsteps, step0, src, nsrc, prb, nprb, probe_out, energy_out, e_io, h_io,
                                      opts, s);
+    if (g->prec == 48 && opts && opts->kernel == 1) return FIT_ERR_UNSUPPORTED;
     return leapfrog_impl<float>(g, dt, nsteps, step0, src, nsrc, prb, nprb, probe_out, energy_out, e_io, h_io, opts,
                                 s);
 }
@@ -1175,6 +1234,7 @@ int paraexp_run(fit_grid *g, double dt, int K, const long *win, const fit_source
     cudaStream_t s = (cudaStream_t)stream;
     if (g->prec == 64)
         return paraexp_impl<double>(g, dt, K, win, src, nsrc, prb, nprb, probe_out, e_final, h_final, e0, h0, opts, s);
+    if (g->prec == 48 && opts && (opts->kernel == 1 || opts->sum_mode == 1)) return FIT_ERR_UNSUPPORTED;
     return paraexp_impl<float>(g, dt, K, win, src, nsrc, prb, nprb, probe_out, e_final, h_final, e0, h0, opts, s);
 }
 
@@ -1223,6 +1283,7 @@ int fit_adjoint_grad(fit_grid *g, double dt, long nsteps, const fit_source *src,
     cudaStream_t s = (cudaStream_t)stream;
     if (g->prec == 64)
         return adjoint_impl<double>(g, dt, nsteps, src, nsrc, prb, nprb, ckpt_every, J_out, grad_eps_r, opts, s);
+    if (g->prec == 48) return FIT_ERR_UNSUPPORTED;
     return adjoint_impl<float>(g, dt, nsteps, src, nsrc, prb, nprb, ckpt_every, J_out, grad_eps_r, opts, s);
 }
 

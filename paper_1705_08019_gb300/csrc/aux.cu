@@ -212,6 +212,47 @@ __global__ void kahan_finish_kernel(long long n, const float *sum, const float *
         out[c] = (double)sum[c] - (double)comp[c];
 }
 
+// FP64 compact (3 components) -> pitched hi/lo floats, zeroing entries that
+// are not degrees of freedom (e: tangential to a wall; h: normal to it)
+__global__ void split_kernel(int nx, int ny, int nz, int pitch, const double *in, float *hi, float *lo, int is_h) {
+    const long long ncell = (long long)nx * ny * nz, ncp = (long long)pitch * ny * nz;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 3 * ncell;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int a = (int)(t / ncell);
+        const long long c = t % ncell;
+        const int i = (int)(c % nx);
+        const int j = (int)((c / nx) % ny);
+        const int k = (int)(c / ((long long)nx * ny));
+        const int q[3] = {i, j, k};
+        const bool dof = is_h ? q[a] > 0 : (q[(a + 1) % 3] > 0 && q[(a + 2) % 3] > 0);
+        const double v = dof ? in[t] : 0.0;
+        const float h = (float)v;
+        const long long o = (long long)a * ncp + ((long long)k * ny + j) * pitch + i;
+        hi[o] = h;
+        lo[o] = (float)(v - (double)h);
+    }
+}
+
+__global__ void join_kernel(int nx, int ny, int nz, int pitch, const float *hi, const float *lo, double *out) {
+    const long long ncell = (long long)nx * ny * nz, ncp = (long long)pitch * ny * nz;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 3 * ncell;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int a = (int)(t / ncell);
+        const long long c = t % ncell;
+        const int i = (int)(c % nx);
+        const int j = (int)((c / nx) % ny);
+        const int k = (int)(c / ((long long)nx * ny));
+        const long long o = (long long)a * ncp + ((long long)k * ny + j) * pitch + i;
+        out[t] = (double)hi[o] + (double)lo[o];
+    }
+}
+
+__global__ void accumulate_pairs_kernel(long long n, const float *hi, const float *lo, double *acc) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x)
+        acc[c] += (double)hi[c] + (double)lo[c];
+}
+
 __global__ void sum_members_kernel(int nmem, long long len, const double *pm, long long stride, double *out) {
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len;
          t += (long long)gridDim.x * blockDim.x) {
@@ -292,6 +333,23 @@ cudaError_t kahan_finish(long long n, const float *sum, const float *comp, doubl
 cudaError_t sum_members(int nmem, long long len, const double *pm, long long stride, double *out, cudaStream_t s) {
     if (len <= 0) return cudaSuccess;
     sum_members_kernel<<<grid_for(len), kThreads, 0, s>>>(nmem, len, pm, stride, out);
+    return cudaGetLastError();
+}
+
+cudaError_t split_pairs(int nx, int ny, int nz, int pitch, const double *in, float *hi, float *lo, int is_h,
+                        cudaStream_t s) {
+    split_kernel<<<grid_for(3LL * nx * ny * nz), kThreads, 0, s>>>(nx, ny, nz, pitch, in, hi, lo, is_h);
+    return cudaGetLastError();
+}
+
+cudaError_t join_pairs(int nx, int ny, int nz, int pitch, const float *hi, const float *lo, double *out,
+                       cudaStream_t s) {
+    join_kernel<<<grid_for(3LL * nx * ny * nz), kThreads, 0, s>>>(nx, ny, nz, pitch, hi, lo, out);
+    return cudaGetLastError();
+}
+
+cudaError_t accumulate_pairs(long long n, const float *hi, const float *lo, double *acc, cudaStream_t s) {
+    accumulate_pairs_kernel<<<grid_for(n), kThreads, 0, s>>>(n, hi, lo, acc);
     return cudaGetLastError();
 }
 

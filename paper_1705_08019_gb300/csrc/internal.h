@@ -140,8 +140,14 @@ cudaError_t launch_batched_f32(const BatchArgs<float> &b, Tile tile, bool lossy,
 int batched_ctas_per_sm_f32(Tile tile, bool lossy);
 bool batched_tile_supported(int tx, int ty);
 // Encode the two tensor maps of a run; returns false if the driver lacks TMA.
+// nstate: components per state block (6, or 12 for compensated fields)
 bool encode_tma_maps(TmaMaps *out, int elem_bytes, int nx, int ny, int nz, int pitch, void *state,
-                     int nblocks, const void *coef, int ncoef, int tx, int ty);
+                     int nblocks, const void *coef, int ncoef, int tx, int ty, int nstate = 6);
+
+// step_comp.cu: compensated FP32 fields (hi + lo pairs, 12-component state blocks)
+cudaError_t launch_step_comp(const StepArgs<float> &a, const TmaMaps &maps, Tile tile, bool lossy, bool mu_array,
+                             bool energy, cudaStream_t s);
+bool comp_tile_supported(int tx, int ty);
 
 // aux.cu
 struct MaterialFlags {
@@ -165,6 +171,12 @@ cudaError_t accumulate_state_kahan(long long n, const T *st, float *sum, float *
 cudaError_t kahan_finish(long long n, const float *sum, const float *comp, double *out, cudaStream_t s);
 cudaError_t sum_members(int nmem, long long len, const double *per_member, long long stride, double *out,
                         cudaStream_t s);
+// compensated fields: FP64 compact (3 components) <-> pitched hi/lo floats
+cudaError_t split_pairs(int nx, int ny, int nz, int pitch, const double *in, float *hi, float *lo, int is_h,
+                        cudaStream_t s);
+cudaError_t join_pairs(int nx, int ny, int nz, int pitch, const float *hi, const float *lo, double *out,
+                       cudaStream_t s);
+cudaError_t accumulate_pairs(long long n, const float *hi, const float *lo, double *acc, cudaStream_t s);
 
 // adjoint.cu
 template <typename T>

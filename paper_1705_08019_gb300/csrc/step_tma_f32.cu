@@ -78,15 +78,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
 }  // namespace
 
 bool encode_tma_maps(TmaMaps *out, int eb, int nx, int ny, int nz, int pitch, void *state, int nblocks,
-                     const void *coef, int ncoef, int tx, int ty) {
+                     const void *coef, int ncoef, int tx, int ty, int nstate) {
     PFN_cuTensorMapEncodeTiled_v12000 fn = encoder();
     if (!fn) return false;
     const CUtensorMapDataType dt = eb == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
     const cuuint64_t row = (cuuint64_t)pitch * eb;
     const cuuint64_t plane = row * ny;
     const cuuint64_t comp = plane * nz;
-    cuuint64_t sdim[5] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, 6, (cuuint64_t)nblocks};
-    cuuint64_t sstr[4] = {row, plane, comp, 6 * comp};
+    cuuint64_t sdim[5] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)nstate, (cuuint64_t)nblocks};
+    cuuint64_t sstr[4] = {row, plane, comp, (cuuint64_t)nstate * comp};
     cuuint32_t sbox[5] = {(cuuint32_t)(tx + 8), (cuuint32_t)(ty + 2), 1, 3, 1};
     cuuint32_t ones[5] = {1, 1, 1, 1, 1};
     if (fn(&out->state, dt, 5, state, sdim, sstr, sbox, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,

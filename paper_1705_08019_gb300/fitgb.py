@@ -308,7 +308,8 @@ class Grid:
         self.dims = tuple(int(v) for v in dims)
         self.spacing = tuple(float(v) for v in spacing)
         self.precision = int(precision)
-        self.dtype = np.float64 if precision == 64 else np.float32
+        # precision 48: compensated FP32 fields (hi + lo float pairs), FP64 I/O
+        self.dtype = np.float64 if precision in (64, 48) else np.float32
         self.handle = fit_grid_create(dims, spacing, eps_r, mu_r, sigma, precision)
 
     @classmethod
