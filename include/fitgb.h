@@ -119,6 +119,11 @@ typedef struct {
 
 /* Grid flags */
 #define FIT_FLAG_NONE 0u
+/* Round the leapfrog coefficients ca, cb, ch to float even on an FP64 grid.
+ * FP32 and compensated grids always store float coefficients; with this flag
+ * an FP64 grid runs exactly their discretization, so comparing with it
+ * measures only the error of the field arithmetic. */
+#define FIT_FLAG_COEF_FLOAT 1u
 
 /* Create a grid and upload its per-cell materials.
  *   eps_r (required), mu_r (NULL = 1), sigma [S/m] (NULL = 0): nx*ny*nz.

@@ -45,6 +45,7 @@ struct fit_grid {
     float *eps = nullptr, *mu = nullptr, *sig = nullptr;
     bool mu_array = false, lossy = false;
     double eps_mu_min = 1.0;
+    unsigned flags = 0;
     // coefficient cache
     bool c_valid = false, c_has_energy = false;
     double c_dt = 0.0;
@@ -152,7 +153,7 @@ int ensure_coeffs(fit_grid *g, double dt, int scheme, bool need_energy, cudaStre
     T *ca = g->lossy ? cb + 3 * g->ncp : nullptr;
     FIT_CHECK(build_coeffs<T>(g->nx, g->ny, g->nz, g->pitch, g->d, g->eps, g->mu, g->sig, dt, scheme, g->mu_array,
                               ca, cb, (T *)g->ch.p, energy ? (T *)g->meps.p : nullptr,
-                              energy ? (T *)g->mmu.p : nullptr, s));
+                              energy ? (T *)g->mmu.p : nullptr, s, (g->flags & FIT_FLAG_COEF_FLOAT) != 0));
     g->stats.kernel_launches += 1;
     g->c_valid = true;
     g->c_dt = dt;
@@ -1127,10 +1128,10 @@ const char *fit_strerror(int st) {
 
 int fit_grid_create(int nx, int ny, int nz, double dx, double dy, double dz, const float *eps_r,
                     const float *mu_r, const float *sigma, int precision, unsigned flags, fit_grid **out) {
-    (void)flags;
     if (!out) return FIT_ERR_ARG;
     *out = nullptr;
     if (nx < 1 || ny < 1 || nz < 1 || !eps_r) return FIT_ERR_ARG;
+    if (flags & ~FIT_FLAG_COEF_FLOAT) return FIT_ERR_ARG;
     if (!(dx > 0) || !(dy > 0) || !(dz > 0) || !std::isfinite(dx) || !std::isfinite(dy) || !std::isfinite(dz))
         return FIT_ERR_ARG;
     if (precision != 32 && precision != 64 && precision != 48) return FIT_ERR_ARG;
@@ -1141,6 +1142,7 @@ int fit_grid_create(int nx, int ny, int nz, double dx, double dy, double dz, con
     g->nx = nx; g->ny = ny; g->nz = nz;
     g->d[0] = dx; g->d[1] = dy; g->d[2] = dz;
     g->prec = precision;
+    g->flags = flags;
     g->ncell = ncell;
     g->pitch = pitch_of(nx);
     g->ncp = (long long)g->pitch * ny * nz;

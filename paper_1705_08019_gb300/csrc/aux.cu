@@ -61,7 +61,7 @@ __global__ void check_kernel(const float *eps, const float *mu, const float *sig
 template <typename T>
 __global__ void coeff_kernel(int nx, int ny, int nz, int pitch, double d0, double d1, double d2, const float *eps,
                              const float *mu, const float *sig, double dt, int scheme, int mu_array,
-                             T *ca, T *cb, T *ch, T *meps, T *mmu) {
+                             T *ca, T *cb, T *ch, T *meps, T *mmu, int round_float) {
     const long long ncell = (long long)pitch * ny * nz;   // padded component stride
     const double d[3] = {d0, d1, d2};
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
@@ -101,6 +101,10 @@ __global__ void coeff_kernel(int nx, int ny, int nz, int pitch, double d0, doubl
                     vca = __dsub_rn(1.0, __dmul_rn(2.0, av));
                     vcb = __ddiv_rn(dt, Me);
                 }
+                if (round_float) {
+                    vca = (double)(float)vca;
+                    vcb = (double)(float)vcb;
+                }
                 if (ca) ca[o] = (T)vca;
                 cb[o] = (T)vcb;
                 if (meps) meps[o] = (T)Me;
@@ -120,7 +124,8 @@ __global__ void coeff_kernel(int nx, int ny, int nz, int pitch, double d0, doubl
                     const double m2 = mu ? (double)mu[rc] : 1.0;
                     const double mt = __ddiv_rn(2.0, __dadd_rn(__ddiv_rn(1.0, m1), __ddiv_rn(1.0, m2)));
                     const double Mm = __ddiv_rn(__dmul_rn(__dmul_rn(kMu0, mt), area), len);
-                    vch = (T)__ddiv_rn(dt, Mm);
+                    const double q = __ddiv_rn(dt, Mm);
+                    vch = (T)(round_float ? (double)(float)q : q);
                     vmm = (T)Mm;
                 }
                 ch[o] = vch;
@@ -136,7 +141,8 @@ __global__ void coeff_kernel(int nx, int ny, int nz, int pitch, double d0, doubl
         const double m1 = mu ? (double)mu[0] : 1.0;
         const double mt = __ddiv_rn(2.0, __dadd_rn(__ddiv_rn(1.0, m1), __ddiv_rn(1.0, m1)));
         const double Mm = __ddiv_rn(__dmul_rn(__dmul_rn(kMu0, mt), area), d[a]);
-        ch[a] = (T)__ddiv_rn(dt, Mm);
+        const double q = __ddiv_rn(dt, Mm);
+        ch[a] = (T)(round_float ? (double)(float)q : q);
         if (mmu) mmu[a] = (T)Mm;
     }
 }
@@ -293,10 +299,11 @@ cudaError_t check_materials(const float *eps, const float *mu, const float *sig,
 template <typename T>
 cudaError_t build_coeffs(int nx, int ny, int nz, int pitch, const double d[3], const float *eps, const float *mu,
                          const float *sig, double dt, int scheme, bool mu_array, T *ca, T *cb, T *ch, T *meps,
-                         T *mmu, cudaStream_t s) {
+                         T *mmu, cudaStream_t s, bool round_float) {
     const long long n = (long long)pitch * ny * nz;
     coeff_kernel<T><<<grid_for(n), kThreads, 0, s>>>(nx, ny, nz, pitch, d[0], d[1], d[2], eps, mu, sig, dt,
-                                                     scheme, mu_array ? 1 : 0, ca, cb, ch, meps, mmu);
+                                                     scheme, mu_array ? 1 : 0, ca, cb, ch, meps, mmu,
+                                                     round_float ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -355,10 +362,10 @@ cudaError_t accumulate_pairs(long long n, const float *hi, const float *lo, doub
 
 template cudaError_t build_coeffs<float>(int, int, int, int, const double *, const float *, const float *,
                                          const float *, double, int, bool, float *, float *, float *, float *,
-                                         float *, cudaStream_t);
+                                         float *, cudaStream_t, bool);
 template cudaError_t build_coeffs<double>(int, int, int, int, const double *, const float *, const float *,
                                           const float *, double, int, bool, double *, double *, double *,
-                                          double *, double *, cudaStream_t);
+                                          double *, double *, cudaStream_t, bool);
 template cudaError_t mask_state<float>(int, int, int, int, float *, float *, cudaStream_t);
 template cudaError_t mask_state<double>(int, int, int, int, double *, double *, cudaStream_t);
 template cudaError_t accumulate_state<float>(long long, const float *, double *, cudaStream_t);

@@ -159,7 +159,7 @@ cudaError_t check_materials(const float *eps, const float *mu, const float *sig,
 template <typename T>
 cudaError_t build_coeffs(int nx, int ny, int nz, int pitch, const double d[3], const float *eps, const float *mu,
                          const float *sig, double dt, int scheme, bool mu_array, T *ca, T *cb, T *ch,
-                         T *meps, T *mmu, cudaStream_t s);
+                         T *meps, T *mmu, cudaStream_t s, bool round_float = false);
 cudaError_t source_table(const fit_source *src_dev, int nsrc, long long base, long long len, double dt,
                          double *amp, cudaStream_t s);
 template <typename T>

@@ -27,6 +27,7 @@ FIT_ERR_NONFINITE = -6
 FIT_ERR_UNSUPPORTED = -7
 
 WAVE_GAUSS_SINE, WAVE_GAUSS, WAVE_SINE = 0, 1, 2
+FIT_FLAG_COEF_FLOAT = 1
 
 EXPORTED = ("fit_grid_create", "fit_grid_destroy", "fit_cfl_dt", "fit_grid_info", "fit_leapfrog_run",
             "paraexp_run", "paraexp_run_batched", "fit_adjoint_grad", "fit_sync", "fit_strerror",
@@ -304,13 +305,13 @@ def fit_sync(g, stream=None):
 class Grid:
     """Owns a fit_grid; field arrays use the compact layout (3, nz, ny, nx)."""
 
-    def __init__(self, dims, spacing, eps_r, mu_r=None, sigma=None, precision=32):
+    def __init__(self, dims, spacing, eps_r, mu_r=None, sigma=None, precision=32, flags=0):
         self.dims = tuple(int(v) for v in dims)
         self.spacing = tuple(float(v) for v in spacing)
         self.precision = int(precision)
         # precision 48: compensated FP32 fields (hi + lo float pairs), FP64 I/O
         self.dtype = np.float64 if precision in (64, 48) else np.float32
-        self.handle = fit_grid_create(dims, spacing, eps_r, mu_r, sigma, precision)
+        self.handle = fit_grid_create(dims, spacing, eps_r, mu_r, sigma, precision, flags)
 
     @classmethod
     def from_workload(cls, w, precision=None):

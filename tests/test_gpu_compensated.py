@@ -65,7 +65,8 @@ def test_compensated_initial_state_and_paraexp():
 
 def test_fullsize_boxes256_compensated_vs_fp64():
     """256^3 lossy boxes, 2000 steps: compensated FP32 against the FP64 path on
-    the same grid; plain FP32 is shown for scale."""
+    the same grid with the same float-rounded coefficients (FIT_FLAG_COEF_FLOAT);
+    plain FP32 is shown for scale."""
     import torch
     w = W.boxes256(nsteps=2000)
     dev = torch.device("cuda")
@@ -73,7 +74,7 @@ def test_fullsize_boxes256_compensated_vs_fp64():
     sig = torch.from_numpy(w.sigma).to(dev)
     out = {}
     for prec in (64, 48, 32):
-        g = fitgb.Grid(w.dims, w.spacing, eps, None, sig, prec)
+        g = fitgb.Grid(w.dims, w.spacing, eps, None, sig, prec, flags=fitgb.FIT_FLAG_COEF_FLOAT)
         dt = w.cfl_fraction * g.cfl_dt()
         T = torch.float32 if prec == 32 else torch.float64
         e = torch.zeros(g.field_shape, dtype=T, device=dev)
@@ -88,3 +89,16 @@ def test_fullsize_boxes256_compensated_vs_fp64():
     e32 = max(relerr(out[32][1], out[64][1]), relerr(out[32][2], out[64][2]), probe_relerr(out[32][0], out[64][0]))
     assert ec <= 1e-9
     assert e32 > 100 * ec
+
+
+def test_coef_float_flag_matches_rounded_oracle():
+    """An FP64 grid with FIT_FLAG_COEF_FLOAT runs the oracle's float-rounded
+    coefficients to FP64 accuracy."""
+    w = W.small_random(dims=(19, 13, 11), nsteps=200, mu=True)
+    dt = w.cfl_fraction * oracle.cfl_dt(w.dims, w.spacing, w.eps_r, w.mu_r)
+    g = fitgb.Grid(w.dims, w.spacing, w.eps_r, w.mu_r, w.sigma, 64, flags=fitgb.FIT_FLAG_COEF_FLOAT)
+    pr, _, e, h = g.leapfrog(dt, w.nsteps, w.sources, w.probes)
+    g.close()
+    og = oracle.OracleGrid(w.dims, w.spacing, w.eps_r, w.mu_r, w.sigma, dt=dt, round32=True)
+    opr, _, oe, oh = og.leapfrog(w.nsteps, w.sources, w.probes)
+    assert probe_relerr(pr, opr) <= 1e-11 and relerr(e, compact(oe)) <= 1e-11 and relerr(h, compact(oh)) <= 1e-11
