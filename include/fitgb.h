@@ -102,6 +102,8 @@ typedef struct {
                                    on the run's stream (fit_last_stats) [0]   */
     int kernel;                 /* step kernel: 1 shared-memory staging by
                                    plain loads, 2 TMA pipeline [0 = 2]        */
+    int stages;                 /* TMA ring depth in planes, 3 or 4 (FP32
+                                   TMA kernels; 0 = the tile's default)       */
 } fit_run_opts;
 
 /* Counters of the last leapfrog / ParaExp run on a grid.  step_ms is the

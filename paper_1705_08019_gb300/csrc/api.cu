@@ -185,6 +185,7 @@ Tile pick_tile(const fit_grid *g, const fit_run_opts *o) {
         t.ty = 8;
     }
     if (o && o->tile_z > 0) t.kz = o->tile_z;
+    if (o && (o->stages == 3 || o->stages == 4)) t.stages = o->stages;
     if (t.kz <= 0) t.kz = 32;
     // small grids: more z chunks so the GPU fills up
     const long long cols = (long long)((g->nx + t.tx - 1) / t.tx) * ((g->ny + t.ty - 1) / t.ty);
@@ -908,6 +909,7 @@ int batched_group(const std::vector<const fit_paraexp_problem *> &probs, bool lo
         tile.ty = opts->tile_y;
     }
     if (opts && opts->tile_z > 0) tile.kz = opts->tile_z;
+    if (opts && (opts->stages == 3 || opts->stages == 4)) tile.stages = opts->stages;
     int nsm = 152;
     {
         int dev = 0;
@@ -984,8 +986,9 @@ int batched_group(const std::vector<const fit_paraexp_problem *> &probs, bool lo
             }
         }
         if (!hit) {
-            const Tile cands[] = {{32, 8, 32, 2}, {32, 8, 16, 2}, {32, 8, 8, 2},  {64, 4, 32, 2},
-                                  {64, 4, 16, 2}, {32, 4, 32, 2}, {32, 4, 16, 2}, {32, 16, 32, 2}};
+            const Tile cands[] = {{32, 8, 32, 2, 4}, {32, 8, 16, 2, 4}, {32, 8, 8, 2, 4},  {32, 8, 32, 2, 3},
+                                  {32, 8, 16, 2, 3}, {64, 4, 32, 2, 4}, {64, 4, 16, 2, 4}, {64, 4, 32, 2, 3},
+                                  {32, 4, 32, 2, 4}, {32, 4, 16, 2, 4}, {32, 16, 32, 2, 3}};
             const int trials = (int)std::min<long long>(3, nit_max);
             float best = 1e30f;
             Tile best_t = tile;

@@ -117,7 +117,8 @@ struct BatchArgs {
 
 struct Tile {
     int tx, ty, kz;
-    int kernel;   // 1: shared-memory staging by plain loads, 2: TMA pipeline
+    int kernel;      // 1: shared-memory staging by plain loads, 2: TMA pipeline
+    int stages = 0;  // TMA ring depth (0: the tile's default)
 };
 
 // step.cu: plain-load staging kernel

@@ -16,13 +16,15 @@ cudaError_t launch_step_tma<float>(const StepArgs<float> &a, const TmaMaps &maps
                                    bool energy, cudaStream_t s) {
     using namespace tma;
 #define FIT_T(TX, TY, S)                                                                   \
-    if (t.tx == TX && t.ty == TY)                                                          \
+    if (t.tx == TX && t.ty == TY && (t.stages == 0 || t.stages == S))                      \
         return lossy ? launch_one<float, TX, TY, S, true>(a, maps, muarr, energy, s)       \
                      : launch_one<float, TX, TY, S, false>(a, maps, muarr, energy, s);
     FIT_T(32, 8, 4)
+    FIT_T(32, 8, 3)
     FIT_T(32, 16, 3)
     FIT_T(32, 4, 4)
     FIT_T(64, 4, 4)
+    FIT_T(64, 4, 3)
 #undef FIT_T
     return cudaErrorInvalidValue;
 }
@@ -34,13 +36,15 @@ bool batched_tile_supported(int tx, int ty) {
 cudaError_t launch_batched_f32(const BatchArgs<float> &b, Tile t, bool lossy, int ctas, cudaStream_t s) {
     using namespace tma;
 #define FIT_T(TX, TY, S)                                                                          \
-    if (t.tx == TX && t.ty == TY)                                                                 \
+    if (t.tx == TX && t.ty == TY && (t.stages == 0 || t.stages == S))                             \
         return lossy ? launch_batched_one<float, TX, TY, S, true>(b, ctas, s)                     \
                      : launch_batched_one<float, TX, TY, S, false>(b, ctas, s);
     FIT_T(32, 8, 4)
+    FIT_T(32, 8, 3)
     FIT_T(32, 16, 3)
     FIT_T(32, 4, 4)
     FIT_T(64, 4, 4)
+    FIT_T(64, 4, 3)
 #undef FIT_T
     return cudaErrorInvalidValue;
 }
@@ -48,12 +52,14 @@ cudaError_t launch_batched_f32(const BatchArgs<float> &b, Tile t, bool lossy, in
 int batched_ctas_per_sm_f32(Tile t, bool lossy) {
     using namespace tma;
 #define FIT_T(TX, TY, S)                                                                          \
-    if (t.tx == TX && t.ty == TY)                                                                 \
+    if (t.tx == TX && t.ty == TY && (t.stages == 0 || t.stages == S))                             \
         return lossy ? batched_occupancy<float, TX, TY, S, true>() : batched_occupancy<float, TX, TY, S, false>();
     FIT_T(32, 8, 4)
+    FIT_T(32, 8, 3)
     FIT_T(32, 16, 3)
     FIT_T(32, 4, 4)
     FIT_T(64, 4, 4)
+    FIT_T(64, 4, 3)
 #undef FIT_T
     return 1;
 }
