@@ -169,6 +169,8 @@ struct MemberSpec {
 
 Tile pick_tile(const fit_grid *g, const fit_run_opts *o) {
     Tile t = g->tile;
+    // FP32 default: 64 x 4 tiles, a 3-plane ring (4 CTAs per SM), 64-plane chunks
+    if (g->prec == 32 && !g->tile_fixed) t = Tile{64, 4, 64, 2, 3};
     if (o && o->kernel > 0) t.kernel = o->kernel;
     if (o && o->tile_x > 0 && o->tile_y > 0) {
         t.tx = o->tile_x;
