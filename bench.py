@@ -50,6 +50,9 @@ def parse():
                     help="run a short untimed case for an ncu capture and exit (no JSON line)")
     ap.add_argument("--ncu-steps", type=int, default=8)
     ap.add_argument("--ncu-members", type=int, default=4)
+    ap.add_argument("--report", action="store_true",
+                    help="accuracy run: FP32 ParaExp of the workload against an FP64 GPU reference "
+                         "(float-rounded coefficients) over the first half of its windows")
     return ap.parse_args()
 
 
@@ -470,8 +473,59 @@ def run_batch(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
+def accuracy_report(args):
+    """One FP32 ParaExp solve of the workload (FP64 superposition) and an FP64
+    sequential leapfrog over the first K/2 windows on the same float-rounded
+    coefficients; prints the probe error over those windows and the timings."""
+    import torch
+    from paper_1705_08019_gb300 import build as B
+    from paper_1705_08019_gb300 import fitgb
+    B.build()
+    fitgb.load()
+    w = load_workload(args.workload)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    eps = torch.from_numpy(w.eps_r).to(dev)
+    sig = torch.from_numpy(w.sigma).to(dev) if w.sigma is not None else None
+    win = w.windows()
+    half = int(win[w.K // 2] - win[0])
+    out = {"workload": w.name, "cells": w.ncells, "nsteps": w.nsteps, "K": w.K, "reference_steps": half}
+    # FP64 reference over the first K/2 windows
+    g = fitgb.fit_grid_create(w.dims, w.spacing, eps, None, sig, 64, fitgb.FIT_FLAG_COEF_FLOAT)
+    dt = w.cfl_fraction * fitgb.fit_cfl_dt(g)
+    ref = torch.zeros((half, len(w.probes)), dtype=torch.float64, device=dev)
+    t0 = time.perf_counter()
+    fitgb.fit_leapfrog_run(g, dt, half, 0, w.sources, w.probes, ref, stream=stream)
+    torch.cuda.synchronize()
+    out["fp64_reference_s"] = time.perf_counter() - t0
+    fitgb.fit_grid_destroy(g)
+    # FP32 ParaExp over all K windows
+    g = fitgb.fit_grid_create(w.dims, w.spacing, eps, None, sig, 32)
+    nt = int(win[-1] - win[0])
+    pr = torch.zeros((nt, len(w.probes)), dtype=torch.float64, device=dev)
+    ef = torch.zeros((3,) + tuple(reversed(w.dims)), dtype=torch.float64, device=dev)
+    hf = torch.zeros_like(ef)
+    t0 = time.perf_counter()
+    fitgb.paraexp_run(g, dt, w.K, win, w.sources, w.probes, pr, ef, hf, opts=fitgb.make_opts(profile=1),
+                      stream=stream)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    st = fitgb.fit_last_stats(g)
+    fitgb.fit_grid_destroy(g)
+    a, b = pr[:half].cpu().numpy(), ref.cpu().numpy()
+    errs = [float(np.linalg.norm(a[:, p] - b[:, p]) / max(np.linalg.norm(b[:, p]), 1e-300)) for p in range(b.shape[1])]
+    out.update({"paraexp_s": sec, "cell_updates": st["cell_updates"], "gcell_per_s": st["cell_updates"] / sec / 1e9,
+                "step_kernel_gbs": st["alg_bytes"] / (st["step_ms"] / 1e3) / 1e9,
+                "probe_relerr_first_half": errs, "max_probe_relerr": max(errs),
+                "peak_device_bytes": torch.cuda.max_memory_allocated(dev)})
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.report:
+        accuracy_report(args)
+        return
     if args.workload == "batch64" and args.impl == "ours" and not args.ncu_case:
         world = int(os.environ.get("WORLD_SIZE", "1"))
         if world > 1:
