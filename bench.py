@@ -204,6 +204,19 @@ def traffic_from_profile():
         return None
 
 
+def reduce_max(x, device=None):
+    """Max of x over the ranks of the default process group (identity without
+    one).  NCCL reduces a device tensor, gloo a host tensor."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return x
+    dev = device if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -270,11 +283,7 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     torch.cuda.synchronize()
     ck = clocks.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(ev0.elapsed_time(ev1) / args.steps, dev)
     cells_per_step = stats[0]["cell_updates"]
     assert cells_per_step == work_of(w), (cells_per_step, work_of(w))
     value = world * cells_per_step / (ms / 1e3) / 1e9
@@ -318,10 +327,7 @@ def run_ours(args, rank, world, local_rank):
         fitgb.paraexp_run(g, dt, w.K, win, w.sources, w.probes, pr_h, ef_h, hf_h)
         e2e_s = time.perf_counter() - t0
         fitgb.fit_grid_destroy(g)
-        if dist is not None:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = reduce_max(e2e_s, dev)
         h2d = sum(a.nbytes for a in (w.eps_r, w.mu_r, w.sigma) if a is not None)
         d2h = pr_h.nbytes + ef_h.nbytes + hf_h.nbytes
         e2e = {"value": world * cells_per_step / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -435,11 +441,7 @@ def run_batch(args, rank, world, local_rank):
     ev1.record(stream)
     torch.cuda.synchronize()
     ck = clocks.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(ev0.elapsed_time(ev1) / args.steps, dev)
     value = world * work / (ms / 1e3) / 1e9
     peak, peak_kind = peaks()
     alg = batch_alg_bytes(ws)
