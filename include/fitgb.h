@@ -104,6 +104,12 @@ typedef struct {
                                    plain loads, 2 TMA pipeline [0 = 2]        */
     int stages;                 /* TMA ring depth in planes, 3 or 4 (FP32
                                    TMA kernels; 0 = the tile's default)       */
+    int debug_wait_limit;       /* test hook: polls before a TMA-kernel wait
+                                   gives up [0 = about a second]              */
+    int debug_extra_tx;         /* test hook: bytes announced on top of the
+                                   first plane's copies of every tile, so its
+                                   wait can never complete and must time out
+                                   (FP32/FP64 TMA kernel) [0]                 */
 } fit_run_opts;
 
 /* Counters of the last leapfrog / ParaExp run on a grid.  step_ms is the

@@ -278,6 +278,8 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
     a.nprb = probes ? nprb : 0;
     for (int q = 0; q < nprb; ++q) a.prb[q] = {prb[q].axis, prb[q].i, prb[q].j, prb[q].k};
     a.err = (int *)g->err.p;
+    a.wait_limit = opts ? std::max(0, opts->debug_wait_limit) : 0;
+    a.extra_tx = opts ? std::max(0, opts->debug_extra_tx) : 0;
     TmaMaps maps;
     if (comp) {
         if (!comp_tile_supported(tile.tx, tile.ty)) tile.tx = 32, tile.ty = 8;

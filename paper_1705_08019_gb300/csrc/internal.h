@@ -80,6 +80,8 @@ struct StepArgs {
     int nprb;
     EdgeRef prb[kMaxPrb];
     int *err;
+    int wait_limit;   // polls before an mbarrier wait gives up (0: default)
+    int extra_tx;     // test hook: bytes announced beyond a tile's first plane
 };
 
 // One grid of a batched launch (device table).

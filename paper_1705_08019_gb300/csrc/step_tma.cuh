@@ -70,8 +70,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 }
 
 // bounded wait; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (int n = 0; n < kWaitLimit; ++n)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int limit = kWaitLimit) {
+    for (int n = 0; n < limit; ++n)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -155,6 +155,8 @@ struct TileJob {
     long long probe_base;
     double *energy_out;       // energy row of this step, or null
     int *err;
+    int wait_limit;           // polls per wait (kWaitLimit when 0)
+    int extra_tx;             // test hook, see StepArgs
 };
 
 // Shared memory of the tile pipeline (dynamic stage ring + these statics).
@@ -217,15 +219,16 @@ __device__ __forceinline__ bool tma_tile(const TileJob<T> &J, const CUtensorMap 
         const int kk = kstart + p;
         unsigned char *st = dsm + (p % S) * G::STAGE;
         uint64_t *b = &sm.bar[p % S];
-        mbar_expect_tx(b, G::TX_BYTES);
+        mbar_expect_tx(b, G::TX_BYTES + (p == 0 ? (uint32_t)J.extra_tx : 0u));
         tma_load_5d(st, tm_state, b, i0 - 4, j0 - 1, kk, 0, J.blk_in);
         tma_load_5d(st + G::H_OFF, tm_state, b, i0 - 4, j0 - 1, kk, 3, J.blk_in);
         tma_load_4d(st + G::C_OFF, tm_coef, b, i0, j0, kk, 0);
     };
     // wait for plane p (its stage's parity flips with every use)
+    const int limit = J.wait_limit > 0 ? J.wait_limit : kWaitLimit;
     auto wait_plane = [&](int p) -> bool {
         const int st = p % S;
-        const bool ok = mbar_wait(&sm.bar[st], (phase >> st) & 1u);
+        const bool ok = mbar_wait(&sm.bar[st], (phase >> st) & 1u, limit);
         if (ok) phase ^= (1u << st);
         return ok;
     };
@@ -319,7 +322,7 @@ __device__ __forceinline__ bool tma_tile(const TileJob<T> &J, const CUtensorMap 
                 sm.sH[0][0][t + 1] = EV(hC, 0, 0, x) - c0 * cxh;
                 sm.sH[2][0][t + 1] = EV(hC, 2, 0, x) - c2 * czh;
             }
-            if (own) {
+            if (own && !bad) {
                 out[3 * ncell + c] = hxn;
                 out[4 * ncell + c] = hyn;
                 out[5 * ncell + c] = hzn;
@@ -456,6 +459,8 @@ __global__ void __launch_bounds__(TX *TY) step_tma_kernel(const __grid_constant_
     J.nprb = a.nprb; J.prb = a.prb; J.probe = mb.probe; J.probe_base = mb.probe_base;
     J.energy_out = (energy && mb.energy) ? mb.energy + (J.step - mb.energy_base) : nullptr;
     J.err = a.err;
+    J.wait_limit = a.wait_limit;
+    J.extra_tx = a.extra_tx;
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) mbar_init(&sm.bar[s], 1);
         mbar_init_fence();
@@ -508,6 +513,8 @@ __global__ void __launch_bounds__(TX *TY) batched_tma_kernel(const __grid_consta
         J.nprb = gd.nprb; J.prb = gd.prb; J.probe = mb.probe; J.probe_base = mb.probe_base;
         J.energy_out = nullptr;
         J.err = b.err;
+        J.wait_limit = 0;
+        J.extra_tx = 0;
         if (!tma_tile<T, TX, TY, S, LOSSY>(J, &b.maps[2 * w.grid], &b.maps[2 * w.grid + 1], dsm, sm, phase))
             return;
     }

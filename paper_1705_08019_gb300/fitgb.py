@@ -54,7 +54,8 @@ class fit_run_opts(ctypes.Structure):
     _fields_ = [("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("tile_z", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("use_graph", ctypes.c_int), ("sigma_scheme", ctypes.c_int),
                 ("sum_mode", ctypes.c_int), ("members_per_pass", ctypes.c_int), ("force_dt", ctypes.c_int),
-                ("profile", ctypes.c_int), ("kernel", ctypes.c_int), ("stages", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("kernel", ctypes.c_int), ("stages", ctypes.c_int),
+                ("debug_wait_limit", ctypes.c_int), ("debug_extra_tx", ctypes.c_int)]
 
 
 class fit_run_stats(ctypes.Structure):

@@ -1,0 +1,37 @@
+"""Failure detection without a GPU fault: every mbarrier wait of the TMA
+step kernel is bounded.  A test hook announces bytes that never arrive, so
+the first plane's wait of every tile runs out; the kernel records the
+timeout, stores nothing, waits (bounded) for its own copies in flight and
+returns.  The host reports FIT_ERR_TIMEOUT and the context stays usable."""
+import numpy as np
+import pytest
+
+from paper_1705_08019_gb300 import fitgb
+from paper_1705_08019_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    fitgb.load()
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_bounded_wait_reports_timeout_and_recovers(precision):
+    w = W.small_random(dims=(16, 12, 10), nsteps=6)
+    g = fitgb.Grid.from_workload(w, precision)
+    dt = 0.9 * g.cfl_dt()
+    ref = g.leapfrog(dt, w.nsteps, w.sources, w.probes)
+    with pytest.raises(fitgb.FitError) as ei:
+        g.leapfrog(dt, w.nsteps, w.sources, w.probes,
+                   opts=fitgb.make_opts(kernel=2, debug_wait_limit=2000, debug_extra_tx=16))
+    assert ei.value.status == fitgb.FIT_ERR_TIMEOUT
+    again = g.leapfrog(dt, w.nsteps, w.sources, w.probes)   # the context is still usable
+    g.close()
+    for a, b in zip(again, ref):
+        if a is not None:
+            assert np.array_equal(a, b)
