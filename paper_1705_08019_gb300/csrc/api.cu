@@ -175,6 +175,7 @@ Tile pick_tile(const fit_grid *g, const fit_run_opts *o) {
     if (o && o->tile_x > 0 && o->tile_y > 0) {
         t.tx = o->tile_x;
         t.ty = o->tile_y;
+        t.stages = 0;   // that tile's default ring depth unless stages is given
     }
     if (g->prec == 48) {
         if (!comp_tile_supported(t.tx, t.ty)) t.tx = 32, t.ty = 8;

@@ -15,6 +15,8 @@ template <>
 cudaError_t launch_step_tma<float>(const StepArgs<float> &a, const TmaMaps &maps, Tile t, bool lossy, bool muarr,
                                    bool energy, cudaStream_t s) {
     using namespace tma;
+    if (t.stages != 0 && !((t.tx == 32 && t.ty == 8) || (t.tx == 64 && t.ty == 4)))
+        t.stages = 0;   // a ring depth this tile has no variant for: its default
 #define FIT_T(TX, TY, S)                                                                   \
     if (t.tx == TX && t.ty == TY && (t.stages == 0 || t.stages == S))                      \
         return lossy ? launch_one<float, TX, TY, S, true>(a, maps, muarr, energy, s)       \
@@ -35,6 +37,7 @@ bool batched_tile_supported(int tx, int ty) {
 
 cudaError_t launch_batched_f32(const BatchArgs<float> &b, Tile t, bool lossy, int ctas, cudaStream_t s) {
     using namespace tma;
+    if (t.stages != 0 && !((t.tx == 32 && t.ty == 8) || (t.tx == 64 && t.ty == 4))) t.stages = 0;
 #define FIT_T(TX, TY, S)                                                                          \
     if (t.tx == TX && t.ty == TY && (t.stages == 0 || t.stages == S))                             \
         return lossy ? launch_batched_one<float, TX, TY, S, true>(b, ctas, s)                     \
@@ -51,6 +54,7 @@ cudaError_t launch_batched_f32(const BatchArgs<float> &b, Tile t, bool lossy, in
 
 int batched_ctas_per_sm_f32(Tile t, bool lossy) {
     using namespace tma;
+    if (t.stages != 0 && !((t.tx == 32 && t.ty == 8) || (t.tx == 64 && t.ty == 4))) t.stages = 0;
 #define FIT_T(TX, TY, S)                                                                          \
     if (t.tx == TX && t.ty == TY && (t.stages == 0 || t.stages == S))                             \
         return lossy ? batched_occupancy<float, TX, TY, S, true>() : batched_occupancy<float, TX, TY, S, false>();
