@@ -457,7 +457,6 @@ def run_batch(args, rank, world, local_rank):
         extras["batched_speedup_vs_plain"] = extras["plain_per_window_ms"] / ms
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        from paper_1705_08019_gb300 import workloads as W
         rate, sec, desc = oracle_sample(ws[0])
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc, "seconds": sec}
     if rank == 0:

@@ -44,6 +44,9 @@
  *   are reported by the next call on that grid or by fit_sync().
  * Errors: every entry point returns a fit_status (0 = success); nothing is
  *   thrown across the ABI.  fit_strerror() describes a status.
+ * Threads: a grid is not thread-safe; calls on one grid must not overlap.
+ *   Different grids may be used from different threads.  The batched entry
+ *   point and the CUDA-graph option synchronize the stream before returning.
  */
 #ifndef FITGB_H
 #define FITGB_H
@@ -152,7 +155,8 @@ int fit_grid_create(int nx, int ny, int nz, double dx, double dy, double dz,
                     const float *eps_r, const float *mu_r, const float *sigma,
                     int precision, unsigned flags, fit_grid **out);
 
-/* Free the grid and every workspace it owns.  NULL is accepted. */
+/* Free the grid and every workspace it owns, after the device has finished
+ * all work (cudaDeviceSynchronize).  NULL is accepted. */
 void fit_grid_destroy(fit_grid *g);
 
 /* Eq. (cfl): dt_CFL = min over cells of sqrt(eps mu / (1/dx^2+1/dy^2+1/dz^2)).

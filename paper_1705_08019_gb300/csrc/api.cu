@@ -1081,36 +1081,28 @@ int batched_group(const std::vector<const fit_paraexp_problem *> &probs, bool lo
     }
     FIT_CHECK(le);
     // probe sums and final fields of each grid
-    bool host_out = false;
     for (int gi = 0; gi < ng; ++gi) {
         BatchHost &h = H[gi];
         fit_grid *g = h.p->grid;
         const fit_paraexp_problem &q = *h.p;
         if (h.probes) {
             FIT_CHECK(sum_members((int)h.specs.size(), h.nt * q.nprb, (const double *)g->pm.p, h.nt * q.nprb, h.pdev, s));
-            if (h.pdev != q.probe_out) {
+            if (h.pdev != q.probe_out)
                 FIT_CHECK(cudaMemcpyAsync(q.probe_out, h.pdev, sizeof(double) * (size_t)h.nt * q.nprb,
                                           cudaMemcpyDeviceToHost, s));
-                host_out = true;
-            }
         }
         const size_t row = (size_t)g->nx * sizeof(double), prow = (size_t)g->pitch * sizeof(double);
         const size_t rows3 = 3 * (size_t)g->ny * g->nz;
-        if (q.e_final) {
+        if (q.e_final)
             FIT_CHECK(cudaMemcpy2DAsync(q.e_final, row, h.ae, prow, row, rows3, kind_from_dev(q.e_final), s));
-            host_out = host_out || !is_device(q.e_final);
-        }
-        if (q.h_final) {
+        if (q.h_final)
             FIT_CHECK(cudaMemcpy2DAsync(q.h_final, row, h.ah, prow, row, rows3, kind_from_dev(q.h_final), s));
-            host_out = host_out || !is_device(q.h_final);
-        }
         g->stats.kernel_launches = g->stats.step_launches;   // shared launches, counted per grid
     }
     // temporary tables are freed when this call returns: wait for the work
     FIT_CHECK(cudaStreamSynchronize(s));
     int rc2 = FIT_OK;
     for (int gi = 0; gi < ng && !rc2; ++gi) rc2 = finish(H[gi].p->grid, s, true);
-    (void)host_out;
     return rc2;
 }
 
