@@ -78,6 +78,8 @@ def _load():
         lib.oracle_paraexp.argtypes = [ctypes.POINTER(_Grid), I, P, P, I, P, I, P, P, P, P, P]
         lib.oracle_adjoint.restype = I
         lib.oracle_adjoint.argtypes = [ctypes.POINTER(_Grid), P, P, I, L, L, P, I, P, I, P, P]
+        lib.oracle_apply_A.restype = I
+        lib.oracle_apply_A.argtypes = [ctypes.POINTER(_Grid), P, P, P, P]
         lib.oracle_constants.restype = None
         lib.oracle_constants.argtypes = [P, P, P]
         _lib = lib
@@ -203,6 +205,17 @@ class OracleGrid:
         if rc:
             raise ValueError(f"oracle_paraexp failed ({rc})")
         return pr, ef, hf
+
+    def apply_A(self, ue, uh):
+        """The skew system matrix of eq. (FIT_ode_2) on transformed unknowns
+        u = [M_mu^{1/2} h, M_eps^{1/2} e]; returns ((A u)_e, (A u)_h)."""
+        ue = np.ascontiguousarray(ue, dtype=np.float64).reshape(self.field_shape)
+        uh = np.ascontiguousarray(uh, dtype=np.float64).reshape(self.field_shape)
+        oe, oh = self.zeros(), self.zeros()
+        rc = _load().oracle_apply_A(ctypes.byref(self._g), _ptr(ue), _ptr(uh), _ptr(oe), _ptr(oh))
+        if rc:
+            raise ValueError(f"oracle_apply_A failed ({rc})")
+        return oe, oh
 
     def adjoint(self, nsteps, sources=(), probes=(), step0=0):
         """J = sum_n sum_p (e_p^n/L_p)^2 and dJ/d eps_r per cell (shape (nz, ny, nx))."""

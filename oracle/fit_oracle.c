@@ -561,3 +561,45 @@ void oracle_constants(double *c0, double *mu0, double *eps0) {
     *mu0 = OR_MU0;
     *eps0 = OR_EPS0;
 }
+
+/* ------------------------------------------------------------------ */
+/* The skew-symmetric system matrix of eq. (FIT_ode_2) acting on the      */
+/* transformed unknowns u = [M_mu^{1/2} h, M_eps^{1/2} e] (Sec. II):       */
+/*   (A u)_h = -M_mu^{-1/2}  C  M_eps^{-1/2} u_e                           */
+/*   (A u)_e =  M_eps^{-1/2} C~ M_mu^{-1/2}  u_h                           */
+/* The sign of the first block row follows the printed A, which agrees   */
+/* with the curl equations (C e = -db/dt, C~h = dd/dt + j) read above;    */
+/* the printed K carries the opposite signs in both block rows.           */
+/* Only degrees of freedom take part (PEC): ue and uh must be zero off     */
+/* them and the outputs are zero there.  Lossless grids only (M_sigma is  */
+/* not part of A).  ue, uh, oe, oh: 3*Np each, canonical layout.          */
+/* ------------------------------------------------------------------ */
+int oracle_apply_A(const or_grid *g, const double *ue, const double *uh, double *oe, double *oh) {
+    int nx = g->nx, ny = g->ny, nz = g->nz;
+    int n[3] = {nx, ny, nz};
+    long Np = np_of(g);
+    double *te = (double *)calloc((size_t)(3 * Np), sizeof(double));
+    double *th = (double *)calloc((size_t)(3 * Np), sizeof(double));
+    if (!te || !th) { free(te); free(th); return -2; }
+    /* te = M_eps^{-1/2} u_e,  th = M_mu^{-1/2} u_h */
+    for (int a = 0; a < 3; ++a)
+        for (int k = 0; k <= nz; ++k)
+            for (int j = 0; j <= ny; ++j)
+                for (int i = 0; i <= nx; ++i) {
+                    int q[3] = {i, j, k};
+                    long p = (long)a * Np + pidx(nx, ny, i, j, k);
+                    if (edge_free(n, a, q)) te[p] = ue[p] / sqrt(g->meps[p]);
+                    if (face_interior(n, a, q)) th[p] = uh[p] / sqrt(g->mmu[p]);
+                }
+    for (int a = 0; a < 3; ++a)
+        for (int k = 0; k <= nz; ++k)
+            for (int j = 0; j <= ny; ++j)
+                for (int i = 0; i <= nx; ++i) {
+                    int q[3] = {i, j, k};
+                    long p = (long)a * Np + pidx(nx, ny, i, j, k);
+                    oe[p] = edge_free(n, a, q) ? curl_h(th, nx, ny, Np, a, q) / sqrt(g->meps[p]) : 0.0;
+                    oh[p] = face_interior(n, a, q) ? -curl_e(te, nx, ny, Np, a, q) / sqrt(g->mmu[p]) : 0.0;
+                }
+    free(te); free(th);
+    return 0;
+}
