@@ -113,7 +113,27 @@ typedef struct {
                                    first plane's copies of every tile, so its
                                    wait can never complete and must time out
                                    (FP32/FP64 TMA kernel) [0]                 */
+    int homogeneous;            /* propagator of the homogeneous ParaExp
+                                   problems: FIT_HOMOG_LEAPFROG, _LEJA or
+                                   _TAYLOR (see paraexp_run) [LEAPFROG]       */
+    int expo_substep;           /* Leja/Taylor: substep length in leapfrog
+                                   steps (q) [0 = planned, fit_expo_plan]     */
+    int expo_degree;            /* Leja/Taylor: even polynomial degree m
+                                   [0 = planned]                              */
+    double expo_tol;            /* Leja/Taylor: backward-error tolerance
+                                   eps_A of ||Delta A|| <= eps_A ||A||
+                                   [0 = 1e-12 for FP64 grids, 1e-6 for FP32]  */
 } fit_run_opts;
+
+/* Propagators of the homogeneous problems w_j (opts->homogeneous). */
+enum {
+    FIT_HOMOG_LEAPFROG = 0, /* leapfrog continued source-free                 */
+    FIT_HOMOG_LEJA = 1,     /* Newton interpolation of exp at conjugate Leja
+                               points of the spectral interval (Sec. III-B)   */
+    FIT_HOMOG_TAYLOR = 2    /* the same with every point at 0: truncated
+                               Taylor series (the method of Sec. III-B that
+                               the paper reports as the slower one)           */
+};
 
 /* Counters of the last leapfrog / ParaExp run on a grid.  step_ms is the
  * summed device time of the fused step launches (only with opts->profile);
@@ -126,6 +146,12 @@ typedef struct {
     long long cell_updates;     /* sum over launches of cells x members      */
     double alg_bytes;           /* algorithmic bytes of the step launches    */
     double step_ms;             /* device time of the step launches (profile)*/
+    long long expo_launches;    /* operator launches of Leja/Taylor runs     */
+    long long expo_applications;/* sum over them of cells x members / cells:
+                                   applications of the operator A per member
+                                   (the SMVP count of the paper)             */
+    double expo_alg_bytes;      /* algorithmic bytes of those launches       */
+    double expo_ms;             /* their device time (opts->profile)         */
 } fit_run_stats;
 
 /* Grid flags */
@@ -200,11 +226,71 @@ int fit_leapfrog_run(fit_grid *g, double dt, long nsteps, long step0,
  * All members are advanced together (coefficients read once per tile for
  * all of them) unless opts->members_per_pass = 1.  Superposition sums are
  * FP64 (or Kahan-compensated FP32 with opts->sum_mode = 1) in a fixed
- * member order, so results do not depend on scheduling. */
+ * member order, so results do not depend on scheduling.
+ * opts->homogeneous = FIT_HOMOG_LEJA or _TAYLOR (lossless FP32/FP64 grids):
+ * member j runs leapfrog over its window only (v_j), ending in
+ * (e^{W_j}, h^{W_j-1/2}); h is brought to the time of e by a half magnetic
+ * step, h^{W_j} = h^{W_j-1/2} - (dt/2) M_mu^{-1} C e^{W_j}, and that state
+ * is propagated to W_K by fit_expo_propagate's propagator (w_{j+1});
+ * w_1 starts from (e0, h0) the same way.  The homogeneous solutions enter
+ * the superposition with e at integer steps and h at half steps (eqs.
+ * averaging1/2): h_final holds them at W_K - 1/2.  sum_mode must be 0 and
+ * members_per_pass is ignored. */
 int paraexp_run(fit_grid *g, double dt, int K, const long *win,
                 const fit_source *src, int nsrc, const fit_probe *prb, int nprb,
                 double *probe_out, double *e_final, double *h_final,
                 const void *e0, const void *h0, const fit_run_opts *opts, void *stream);
+
+/* Exponential propagators (Sec. III-B, "Approximation of the matrix
+ * exponential").  On a lossless grid the transformed system of eq.
+ * (FIT_ode_2) has the skew matrix A, whose spectrum lies in i[-beta, beta],
+ * beta = ||A||_2 <= 2/dt_CFL (the bound behind eq. (cfl)).  With
+ * X = dt_CFL A, a substep of q leapfrog steps is exp(c X), c = q dt/dt_CFL,
+ * replaced by the Newton interpolant p_m of exp(c z) at m+1 points of
+ * i[-2, 2]:
+ *   Leja:   xi_0 = 0, then conjugate pairs +-i eta_j, eta_j the first
+ *           maximiser over eta = 2l/2^15 (l = 0..2^15) of the product of
+ *           distances to the points chosen before;
+ *   Taylor: every point 0.
+ * Applied in real arithmetic as
+ *   p_m(X) b = b + sum_{j=1}^{m/2} R_{j-1}(X) b (alpha_j + gamma_j X),
+ *   R_0 = X, R_j = (X^2 + eta_j^2) R_{j-1},
+ * alpha_j = d_{2j-1} - i eta_j d_{2j} and gamma_j = d_{2j}, d_k the divided
+ * differences (both real for conjugate points).  Since polynomials of A and
+ * of M^{-1}K are similar, the library applies X in the untransformed
+ * voltages: X (e, h) = (dt_CFL/dt) (cb C~h, -ch C e) on a lossless grid.
+ *
+ * fit_expo_plan: the substep q (leapfrog steps) and degree m for
+ * dt_ratio = dt/dt_CFL, the tolerance eps_A and the field precision
+ * (32, 64).  The condition ||Delta A|| <= eps_A ||A|| of Sec. III-D, with
+ * ||A|| replaced by beta, holds for a normal A when
+ *   max_{z in i[-2,2]} |log(p_m(z) e^{-cz})| + u_p H_m <= 2 c eps_A,
+ * evaluated at z = i 2l/4096 (l = 0..4096); H_m = max_z sum_k |d_k w_k(z)|
+ * bounds the rounding of the Newton sum (u_p: unit roundoff of the
+ * precision); the same must hold with tau c for every output fraction
+ * tau = i/q.  Over q with q dt/dt_CFL <= 32 and even m <= 120 the least m/q
+ * wins (ties: smaller q).  Host only (no device work); FIT_ERR_ARG if no
+ * pair meets the tolerance. */
+int fit_expo_plan(int kind, double dt_ratio, double tol, int precision, int *substep, int *degree);
+
+/* The real coefficients alpha_j, gamma_j, eta_j^2 (j = 1..degree/2) of the
+ * interpolant of exp(a z) of the given kind and even degree (a = tau c).
+ * Divided differences are the first column of exp(a Z), Z the bidiagonal
+ * matrix of the points (Opitz), by scaling and squaring.  Host only. */
+int fit_expo_coeffs(int kind, int degree, double a, double *alpha, double *gamma, double *eta2);
+
+/* w(t) = exp((t - t0) A) (e, h): propagate a synchronised state (e and h at
+ * the same time t0) over nsteps leapfrog steps with the propagator
+ * opts->homogeneous (LEJA or TAYLOR; LEAPFROG is FIT_ERR_ARG).
+ *   e_io, h_io: 3*nx*ny*nz float/double (grid precision), the state at t0
+ *     on entry and at t0 + nsteps dt on exit.
+ *   probe_out: nsteps*nprb doubles, row n = e at t0 + (n+1) dt (dense
+ *     output: the Newton basis of a substep serves every step inside it),
+ *     or NULL.
+ * Lossless FP32/FP64 grids only (FIT_ERR_UNSUPPORTED otherwise). */
+int fit_expo_propagate(fit_grid *g, double dt, long nsteps, const fit_probe *prb, int nprb,
+                       double *probe_out, void *e_io, void *h_io, const fit_run_opts *opts,
+                       void *stream);
 
 /* One ParaExp problem of a batch. */
 typedef struct {

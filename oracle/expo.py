@@ -294,10 +294,11 @@ def half_h_step(og, e, h):
 
 
 def paraexp(og, K, win, sources=(), probes=(), kind="leja", q=None, m=None, tol=1e-12, precision=64,
-            dt_cfl=None):
+            dt_cfl=None, e0=None, h0=None):
     """ParaExp (Algorithm 1) with leapfrog window problems v_j and the
     homogeneous problems w_{j+1} = exp((t - T_j) A) v_j(T_j) by the
-    propagator above; zero initial value (w_1 = 0).  Returns
+    propagator above.  The initial value (e0, h0) = (e^{W_0}, h^{W_0-1/2})
+    (zero if both are None) gives w_1, synchronised like the v_j.  Returns
     (probes[n, p] for absolute steps win[0]+1..win[K], e(T), h(T - dt/2))."""
     from . import cfl_dt
     win = [int(v) for v in win]
@@ -320,6 +321,14 @@ def paraexp(og, K, win, sources=(), probes=(), kind="leja", q=None, m=None, tol=
         p2, ew, hw = propagate(og, win[K] - hi, e, hs, probes, kind, q, m, tol, precision, dt_cfl,
                                stagger_h=True)
         pr[hi - win[0]:] += p2
+        e_fin += ew
+        h_fin += hw
+    if e0 is not None or h0 is not None:
+        e = og.zeros() if e0 is None else np.asarray(e0, dtype=float)
+        h = og.zeros() if h0 is None else np.asarray(h0, dtype=float)
+        p2, ew, hw = propagate(og, nt, e, half_h_step(og, e, h), probes, kind, q, m, tol, precision, dt_cfl,
+                               stagger_h=True)
+        pr += p2
         e_fin += ew
         h_fin += hw
     return pr, e_fin, h_fin

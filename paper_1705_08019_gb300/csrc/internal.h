@@ -181,6 +181,60 @@ cudaError_t join_pairs(int nx, int ny, int nz, int pitch, const float *hi, const
                        cudaStream_t s);
 cudaError_t accumulate_pairs(long long n, const float *hi, const float *lo, double *acc, cudaStream_t s);
 
+// expo_plan.cu: host side of the Leja / Taylor propagators
+constexpr int kExpoMaxDegree = 120;
+// (q, m) for dt/dt_CFL = u; FIT_OK or FIT_ERR_ARG.  Cached per argument set.
+int expo_plan(int kind, double u, double tol, int precision, int *q, int *m);
+// real pair coefficients of the interpolant of exp(a z): alpha[J], gamma[J], eta2[J], J = m/2
+int expo_pair_coeffs(int kind, int m, double a, double *alpha, double *gamma, double *eta2);
+
+// expo.cu: one member of an exponential propagation
+template <typename T>
+struct ExpoMember {
+    T *P;                // accumulator; holds b at a substep's start (6-component pitched block)
+    T *R;                // R_{j-1}(X) b
+    T *Y;                // X R_{j-1}(X) b
+    int nsub;            // substeps of this member
+    const double *fin;   // final substep: [J][4] = alpha_e, gamma_e, alpha_h, gamma_h
+    double *basis;       // probe basis: [substep][m+1][nprb] (e at the probe edges)
+};
+
+enum ExpoMode { kExpoInit = 0, kExpoPair1 = 1, kExpoPair2 = 2, kExpoSync = 3 };
+
+template <typename T>
+struct ExpoArgs {
+    int nx, ny, nz, pitch;
+    long long ncp;          // padded component stride
+    int kz, nchunk;         // z planes per block, chunks along z
+    const T *cb;            // 3 components (zero off the degrees of freedom)
+    const T *ch;            // 3 values (uniform mu) or 3 components
+    double kappa;           // dt_CFL / dt
+    const ExpoMember<T> *mem;
+    int nmem;               // active members (table prefix)
+    int mode;               // ExpoMode
+    int pair;               // j = 1..J (pair launches)
+    int substep;
+    const double *reg;      // [J][2] = alpha, gamma at tau = 1
+    double eta2;            // eta_j^2 (second pair launch)
+    double sync;            // dt/(2 dt_CFL): half magnetic step in units of X
+    int m1;                 // m + 1 (probe basis rows per substep)
+    int nprb;
+    EdgeRef prb[kMaxPrb];
+};
+
+template <typename T>
+cudaError_t launch_expo(const ExpoArgs<T> &a, bool mu_array, cudaStream_t s);
+// probe rows of the Newton basis after an init or a first pair launch
+template <typename T>
+cudaError_t launch_expo_gather(const ExpoArgs<T> &a, cudaStream_t s);
+// dense output: out[m*ostride + (row0[m] + r)*nprb + p] = sum_k D[(r % q)*m1 + k] basis_m[(r/q)*m1 + k][p]
+// for r < nrem[m]
+cudaError_t launch_expo_dense(int nmem, const double *const *basis, const long long *nrem, const long long *row0,
+                              long long max_rows, int q, int m1, int nprb, const double *D, double *out,
+                              long long ostride, cudaStream_t s);
+// out[t] += sum_m pm[m*stride + t], members in order
+cudaError_t add_members(int nmem, long long len, const double *pm, long long stride, double *out, cudaStream_t s);
+
 // adjoint.cu
 template <typename T>
 cudaError_t adjoint_init(const fit_probe *prb, int nprb, const double d[3], const double *probe_last, const T *cb,

@@ -29,9 +29,13 @@ FIT_ERR_UNSUPPORTED = -7
 WAVE_GAUSS_SINE, WAVE_GAUSS, WAVE_SINE = 0, 1, 2
 FIT_FLAG_COEF_FLOAT = 1
 
+HOMOG_LEAPFROG, HOMOG_LEJA, HOMOG_TAYLOR = 0, 1, 2
+HOMOG = {"leapfrog": HOMOG_LEAPFROG, "leja": HOMOG_LEJA, "taylor": HOMOG_TAYLOR}
+
 EXPORTED = ("fit_grid_create", "fit_grid_destroy", "fit_cfl_dt", "fit_grid_info", "fit_leapfrog_run",
             "paraexp_run", "paraexp_run_batched", "fit_adjoint_grad", "fit_sync", "fit_strerror",
-            "fit_version", "fit_last_stats", "fit_leapfrog_run_static")
+            "fit_version", "fit_last_stats", "fit_leapfrog_run_static", "fit_expo_plan", "fit_expo_coeffs",
+            "fit_expo_propagate")
 
 
 class FitError(RuntimeError):
@@ -55,12 +59,16 @@ class fit_run_opts(ctypes.Structure):
                 ("autotune", ctypes.c_int), ("use_graph", ctypes.c_int), ("sigma_scheme", ctypes.c_int),
                 ("sum_mode", ctypes.c_int), ("members_per_pass", ctypes.c_int), ("force_dt", ctypes.c_int),
                 ("profile", ctypes.c_int), ("kernel", ctypes.c_int), ("stages", ctypes.c_int),
-                ("debug_wait_limit", ctypes.c_int), ("debug_extra_tx", ctypes.c_int)]
+                ("debug_wait_limit", ctypes.c_int), ("debug_extra_tx", ctypes.c_int),
+                ("homogeneous", ctypes.c_int), ("expo_substep", ctypes.c_int), ("expo_degree", ctypes.c_int),
+                ("expo_tol", ctypes.c_double)]
 
 
 class fit_run_stats(ctypes.Structure):
     _fields_ = [("step_launches", ctypes.c_longlong), ("kernel_launches", ctypes.c_longlong),
-                ("cell_updates", ctypes.c_longlong), ("alg_bytes", ctypes.c_double), ("step_ms", ctypes.c_double)]
+                ("cell_updates", ctypes.c_longlong), ("alg_bytes", ctypes.c_double), ("step_ms", ctypes.c_double),
+                ("expo_launches", ctypes.c_longlong), ("expo_applications", ctypes.c_longlong),
+                ("expo_alg_bytes", ctypes.c_double), ("expo_ms", ctypes.c_double)]
 
 
 class fit_paraexp_problem(ctypes.Structure):
@@ -103,6 +111,12 @@ def load():
         lib.fit_adjoint_grad.restype = I
         lib.fit_leapfrog_run_static.argtypes = [I, I, I, D, D, D, P, P, D, L, L, P, I, P, I, P, P, P, P]
         lib.fit_leapfrog_run_static.restype = I
+        lib.fit_expo_plan.argtypes = [I, D, D, I, ctypes.POINTER(I), ctypes.POINTER(I)]
+        lib.fit_expo_plan.restype = I
+        lib.fit_expo_coeffs.argtypes = [I, I, D, P, P, P]
+        lib.fit_expo_coeffs.restype = I
+        lib.fit_expo_propagate.argtypes = [P, D, L, P, I, P, P, P, P, P]
+        lib.fit_expo_propagate.restype = I
         lib.fit_last_stats.argtypes = [P, ctypes.POINTER(fit_run_stats)]
         lib.fit_last_stats.restype = I
         lib.fit_sync.argtypes = [P, P]
@@ -170,9 +184,13 @@ def probes_array(probes):
 
 
 def make_opts(**kw):
+    """fit_run_opts from keyword arguments; homogeneous may be given by name
+    ("leapfrog", "leja", "taylor")."""
     o = fit_run_opts()
     for k, v in kw.items():
-        setattr(o, k, int(v))
+        if k == "homogeneous" and isinstance(v, str):
+            v = HOMOG[v]
+        setattr(o, k, float(v) if k == "expo_tol" else int(v))
     return o
 
 
@@ -288,11 +306,39 @@ def fit_leapfrog_run_static(dims, spacing, eps_r, sigma, dt, nsteps, step0=0, so
     _check(rc, "fit_leapfrog_run_static")
 
 
+def fit_expo_plan(kind, dt_ratio, tol, precision=64):
+    """(substep q, degree m) of the Leja/Taylor propagator (host only)."""
+    q, m = ctypes.c_int(), ctypes.c_int()
+    _check(load().fit_expo_plan(HOMOG.get(kind, kind), float(dt_ratio), float(tol), int(precision),
+                                ctypes.byref(q), ctypes.byref(m)), "fit_expo_plan")
+    return q.value, m.value
+
+
+def fit_expo_coeffs(kind, degree, a):
+    """(alpha, gamma, eta^2) of the real Newton form of the interpolant of
+    exp(a z), each of length degree/2 (host only)."""
+    J = int(degree) // 2
+    al, ga, et = np.zeros(J), np.zeros(J), np.zeros(J)
+    _check(load().fit_expo_coeffs(HOMOG.get(kind, kind), int(degree), float(a), _addr(al), _addr(ga), _addr(et)),
+           "fit_expo_coeffs")
+    return al, ga, et
+
+
+def fit_expo_propagate(g, dt, nsteps, probes=(), probe_out=None, e_io=None, h_io=None, opts=None, stream=None):
+    prb = probes_array(probes)
+    rc = load().fit_expo_propagate(g, float(dt), int(nsteps), ctypes.cast(prb, ctypes.c_void_p), len(probes),
+                                   _addr(probe_out), _addr(e_io), _addr(h_io),
+                                   ctypes.byref(opts) if opts is not None else None, _stream(stream))
+    _check(rc, "fit_expo_propagate")
+
+
 def fit_last_stats(g):
     st = fit_run_stats()
     _check(load().fit_last_stats(g, ctypes.byref(st)), "fit_last_stats")
     return dict(step_launches=st.step_launches, kernel_launches=st.kernel_launches,
-                cell_updates=st.cell_updates, alg_bytes=st.alg_bytes, step_ms=st.step_ms)
+                cell_updates=st.cell_updates, alg_bytes=st.alg_bytes, step_ms=st.step_ms,
+                expo_launches=st.expo_launches, expo_applications=st.expo_applications,
+                expo_alg_bytes=st.expo_alg_bytes, expo_ms=st.expo_ms)
 
 
 def fit_sync(g, stream=None):
@@ -346,6 +392,16 @@ class Grid:
             h0 = np.ascontiguousarray(h0, dtype=self.dtype)
         paraexp_run(self.handle, dt, K, win, sources, probes, pr, ef, hf, e0, h0, opts)
         return pr, ef, hf
+
+    def expo_propagate(self, dt, nsteps, e, h, probes=(), kind="leja", tol=0.0, q=0, m=0):
+        """Host-side convenience: exp(nsteps dt A) of a synchronised state;
+        returns (probes[n, p], e, h) as numpy."""
+        e = np.array(e, dtype=self.dtype)
+        h = np.array(h, dtype=self.dtype)
+        pr = np.zeros((nsteps, len(probes))) if probes else None
+        opts = make_opts(homogeneous=kind, expo_tol=tol, expo_substep=q, expo_degree=m)
+        fit_expo_propagate(self.handle, dt, nsteps, probes, pr, e, h, opts)
+        return pr, e, h
 
     def adjoint(self, dt, nsteps, sources=(), probes=(), ckpt_every=0, opts=None):
         nx, ny, nz = self.dims

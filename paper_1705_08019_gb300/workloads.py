@@ -213,6 +213,17 @@ def small_random(dims=(12, 10, 8), spacing=(1e-3, 1.2e-3, 0.9e-3), seed: int = S
                     precision=precision)
 
 
+def random_state(dims, seed: int = SEED + 7, dtype=np.float64):
+    """Seeded normal (e, h) in the compact layout (3, nz, ny, nx): an initial
+    value for propagation tests (entries off the degrees of freedom are
+    ignored by both the library and the oracle)."""
+    rng = _rng(seed)
+    nx, ny, nz = dims
+    e = rng.standard_normal((3, nz, ny, nx)).astype(dtype)
+    h = rng.standard_normal((3, nz, ny, nx)).astype(dtype)
+    return e, h
+
+
 WORKLOADS = {
     "cavity16": cavity16,
     "boxes256": boxes256,
