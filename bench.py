@@ -46,10 +46,15 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--compare-plain", action="store_true",
                     help="also time the K windows run one after another (members_per_pass=1)")
-    ap.add_argument("--ncu-case", choices=["leapfrog", "paraexp"], default=None,
+    ap.add_argument("--ncu-case", choices=["leapfrog", "paraexp", "expo"], default=None,
                     help="run a short untimed case for an ncu capture and exit (no JSON line)")
     ap.add_argument("--ncu-steps", type=int, default=8)
     ap.add_argument("--ncu-members", type=int, default=4)
+    ap.add_argument("--expo-report", action="store_true",
+                    help="ParaExp with Leja homogeneous problems against ParaExp with leapfrog ones on a "
+                         "lossless workload (default boxes256lossless): times, operator rate, roofline, "
+                         "error against FP64 runs")
+    ap.add_argument("--expo-tol", type=float, default=1e-6)
     ap.add_argument("--report", action="store_true",
                     help="accuracy run: FP32 ParaExp of the workload against an FP64 GPU reference "
                          "(float-rounded coefficients) over the first half of its windows")
@@ -66,6 +71,10 @@ def load_workload(name):
         return W.cavity16()
     if name == "boxes512":
         return W.boxes512()
+    if name == "boxes256lossless":
+        return W.boxes256_lossless()
+    if name == "wave2d":
+        return W.wave2d()
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -369,6 +378,12 @@ def ncu_case(args):
     s = torch.cuda.current_stream(dev)
     if args.ncu_case == "leapfrog":
         fitgb.fit_leapfrog_run(g, dt, args.ncu_steps, 0, w.sources, w.probes, None, None, None, None, None, s)
+    elif args.ncu_case == "expo":
+        # one Leja substep of degree 8 over --ncu-steps steps from a seeded state
+        from paper_1705_08019_gb300 import workloads as W
+        e0, h0 = (torch.from_numpy(a).to(dev) for a in W.random_state(w.dims, dtype=np.float32))
+        opts = fitgb.make_opts(homogeneous="leja", expo_substep=args.ncu_steps, expo_degree=8)
+        fitgb.fit_expo_propagate(g, dt, args.ncu_steps, w.probes, None, e0, h0, opts, s)
     else:
         K = args.ncu_members
         win = np.array([j for j in range(K)] + [args.ncu_steps], dtype=np.int64)
@@ -522,8 +537,80 @@ def accuracy_report(args):
     print(json.dumps(out), flush=True)
 
 
+def expo_report(args):
+    """ParaExp of a lossless workload twice in FP32 -- homogeneous problems by
+    leapfrog and by Leja interpolation (Sec. III-B) -- plus FP64 runs of both
+    (the Leja one with the FP64 tolerance) as references.  Prints one JSON
+    object: wall times, the operator kernel's application rate and
+    algorithmic bandwidth, and probe errors."""
+    import torch
+    from paper_1705_08019_gb300 import build as B
+    from paper_1705_08019_gb300 import fitgb
+    B.build()
+    fitgb.load()
+    name = args.workload if args.workload != "boxes256" else "boxes256lossless"
+    w = load_workload(name)
+    if w.sigma is not None:
+        raise SystemExit("the exponential propagators need a lossless workload")
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    eps = torch.from_numpy(w.eps_r).to(dev)
+    win = w.windows()
+    nt = int(win[-1] - win[0])
+    out = {"workload": w.name, "cells": w.ncells, "nsteps": w.nsteps, "K": w.K, "expo_tol_fp32": args.expo_tol}
+    peak = peaks()[0]
+
+    def run(prec, homog, tol):
+        g = fitgb.fit_grid_create(w.dims, w.spacing, eps, None, None, prec)
+        dt = w.cfl_fraction * fitgb.fit_cfl_dt(g)
+        pr = torch.zeros((nt, len(w.probes)), dtype=torch.float64, device=dev)
+        opts = fitgb.make_opts(profile=1, homogeneous=homog, expo_tol=tol)
+        fitgb.paraexp_run(g, dt, w.K, win, w.sources, w.probes, pr, opts=opts, stream=stream)   # plans, warms up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fitgb.paraexp_run(g, dt, w.K, win, w.sources, w.probes, pr, opts=opts, stream=stream)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        st = fitgb.fit_last_stats(g)
+        fitgb.fit_grid_destroy(g)
+        return pr.cpu().numpy(), sec, st, dt
+
+    def rel(a, b):
+        return max(float(np.linalg.norm(a[:, p] - b[:, p]) / max(np.linalg.norm(b[:, p]), 1e-300))
+                   for p in range(b.shape[1]))
+
+    p_lf, s_lf, st_lf, dt = run(32, "leapfrog", 0.0)
+    p_lj, s_lj, st_lj, _ = run(32, "leja", args.expo_tol)
+    q, m = fitgb.fit_expo_plan("leja", w.cfl_fraction, args.expo_tol, 32)
+    p_lf64, _, _, _ = run(64, "leapfrog", 0.0)
+    p_lj64, s_lj64, st_lj64, _ = run(64, "leja", 1e-12)
+    out.update({
+        "leapfrog_homogeneous": {"seconds": s_lf, "cell_updates": st_lf["cell_updates"],
+                                 "gcell_per_s": st_lf["cell_updates"] / s_lf / 1e9,
+                                 "probe_relerr_vs_fp64": rel(p_lf, p_lf64)},
+        "leja_homogeneous": {"seconds": s_lj, "substep": q, "degree": m,
+                             "operator_applications": st_lj["expo_applications"],
+                             "expo_launches": st_lj["expo_launches"],
+                             "gcell_applications_per_s": st_lj["expo_applications"] * w.ncells / (st_lj["expo_ms"] / 1e3) / 1e9,
+                             "expo_kernel_gbs": st_lj["expo_alg_bytes"] / (st_lj["expo_ms"] / 1e3) / 1e9,
+                             "expo_kernel_frac_of_measured_hbm": st_lj["expo_alg_bytes"] / (st_lj["expo_ms"] / 1e3) / 1e9 / peak,
+                             "expo_share_of_run": st_lj["expo_ms"] / 1e3 / s_lj,
+                             "leapfrog_window_seconds": st_lj["step_ms"] / 1e3,
+                             "probe_relerr_vs_fp64_leja": rel(p_lj, p_lj64),
+                             "probe_relerr_vs_fp64_leapfrog_paraexp": rel(p_lj, p_lf64)},
+        "leja_fp64": {"seconds": s_lj64, "operator_applications": st_lj64["expo_applications"],
+                      "probe_relerr_vs_fp64_leapfrog_paraexp": rel(p_lj64, p_lf64)},
+        "leja_over_leapfrog_time": s_lj / s_lf,
+        "peak_hbm_gbs": peak,
+    })
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.expo_report:
+        expo_report(args)
+        return
     if args.report:
         accuracy_report(args)
         return

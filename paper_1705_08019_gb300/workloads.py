@@ -123,7 +123,7 @@ def cavity16(seed: int = SEED, nsteps: int = 2000) -> Workload:
 
 
 def boxes(n_side: int = 256, seed: int = SEED, nsteps: int = 20000, K: int = 16,
-          side_scale: float = 1.0, name: str = "boxes256", nboxes: int = 40) -> Workload:
+          side_scale: float = 1.0, name: str = "boxes256", nboxes: int = 40, lossy: bool = True) -> Workload:
     rng = _rng(seed)
     n = (n_side, n_side, n_side)
     lo = max(1, int(round(8 * side_scale)))
@@ -133,13 +133,19 @@ def boxes(n_side: int = 256, seed: int = SEED, nsteps: int = 20000, K: int = 16,
     d = 0.5e-3
     c = n_side // 2
     return Workload(
-        name=name, dims=n, spacing=(d, d, d), eps_r=eps, mu_r=None, sigma=sigma,
+        name=name, dims=n, spacing=(d, d, d), eps_r=eps, mu_r=None, sigma=sigma if lossy else None,
         sources=[band_source(2, c, c, c, d, 10.0)], probes=_centre_probes(n),
         nsteps=nsteps, cfl_fraction=0.95, K=K, precision=32)
 
 
 def boxes256(seed: int = SEED, nsteps: int = 20000, n_side: int = 256) -> Workload:
     return boxes(n_side=n_side, seed=seed, nsteps=nsteps, K=16, name="boxes256")
+
+
+def boxes256_lossless(seed: int = SEED, nsteps: int = 2000, n_side: int = 256) -> Workload:
+    """The 256^3 boxes without conductivity (the same eps_r): the exponential
+    propagators need a lossless grid."""
+    return boxes(n_side=n_side, seed=seed, nsteps=nsteps, K=16, name="boxes256lossless", lossy=False)
 
 
 def boxes512(seed: int = SEED, nsteps: int = 100000, n_side: int = 512) -> Workload:
@@ -229,5 +235,6 @@ WORKLOADS = {
     "boxes256": boxes256,
     "adjoint128": adjoint128,
     "boxes512": boxes512,
+    "boxes256lossless": boxes256_lossless,
     "wave2d": wave2d,
 }
