@@ -752,6 +752,7 @@ int expo_members(fit_grid *g, double dt, const ExpoParams &X, const std::vector<
     const long long cols = (long long)((g->nx + 31) / 32) * ((g->ny + 7) / 8);
     a.kz = 32;
     while (a.kz > 4 && cols * ((g->nz + a.kz - 1) / a.kz) < 8 * 152) a.kz /= 2;
+    if (opts && opts->tile_z > 0) a.kz = std::min(opts->tile_z, g->nz);
     a.nchunk = (g->nz + a.kz - 1) / a.kz;
     if ((long long)a.nchunk * nmem > 65535) return FIT_ERR_UNSUPPORTED;
 

@@ -43,7 +43,11 @@ __global__ void __launch_bounds__(kEx * kEy) expo_kernel(const ExpoArgs<T> a) {
     const int k0 = chunk * a.kz;
     const int k1 = min(a.nz, k0 + a.kz);
 
-    const T *x = MODE == kExpoPair1 ? M.R : MODE == kExpoPair2 ? M.Y : M.P;
+    // the stencil input is not written by this launch (the synchronisation
+    // writes only the h of its own cell, after reading it): read-only loads
+    const T *__restrict__ x = MODE == kExpoPair1 ? M.R : MODE == kExpoPair2 ? M.Y : M.P;
+    const T *__restrict__ cb = a.cb;
+    const T *__restrict__ chp = a.ch;
     const T kap = (T)a.kappa;
 
     T al_e = T(0), ga_e = T(0), al_h = T(0), ga_h = T(0);
@@ -58,28 +62,28 @@ __global__ void __launch_bounds__(kEx * kEy) expo_kernel(const ExpoArgs<T> a) {
     }
     const T eta2 = (T)a.eta2;
     const T sync = (T)a.sync;
-    const T chs0 = MUARR ? T(0) : a.ch[0], chs1 = MUARR ? T(0) : a.ch[1], chs2 = MUARR ? T(0) : a.ch[2];
+    const T chs0 = MUARR ? T(0) : __ldg(chp), chs1 = MUARR ? T(0) : __ldg(chp + 1), chs2 = MUARR ? T(0) : __ldg(chp + 2);
 
     const bool xup = i + 1 < a.nx, yup = j + 1 < a.ny, xdn = i > 0, ydn = j > 0;
     long long c = (long long)i + (long long)pitch * j + plane * k0;
     // carried along z: h_x, h_y of plane k-1 and e_x, e_y of plane k
-    T hx_m = (kNeedCh && k0 > 0) ? x[3 * n + c - plane] : T(0);
-    T hy_m = (kNeedCh && k0 > 0) ? x[4 * n + c - plane] : T(0);
-    T ex_0 = x[c], ey_0 = x[n + c];
+    T hx_m = (kNeedCh && k0 > 0) ? __ldg(x + 3 * n + c - plane) : T(0);
+    T hy_m = (kNeedCh && k0 > 0) ? __ldg(x + 4 * n + c - plane) : T(0);
+    T ex_0 = __ldg(x + c), ey_0 = __ldg(x + n + c);
     for (int k = k0; k < k1; ++k, c += plane) {
         const bool zup = k + 1 < a.nz;
-        const T ex_p = zup ? x[c + plane] : T(0);
-        const T ey_p = zup ? x[n + c + plane] : T(0);
-        const T ez = x[2 * n + c];
-        const T hx = x[3 * n + c], hy = x[4 * n + c], hz = x[5 * n + c];
-        const T ey_ip = xup ? x[n + c + 1] : T(0);
-        const T ez_ip = xup ? x[2 * n + c + 1] : T(0);
-        const T ex_jp = yup ? x[c + pitch] : T(0);
-        const T ez_jp = yup ? x[2 * n + c + pitch] : T(0);
-        const T hy_im = (kNeedCh && xdn) ? x[4 * n + c - 1] : T(0);
-        const T hz_im = (kNeedCh && xdn) ? x[5 * n + c - 1] : T(0);
-        const T hx_jm = (kNeedCh && ydn) ? x[3 * n + c - pitch] : T(0);
-        const T hz_jm = (kNeedCh && ydn) ? x[5 * n + c - pitch] : T(0);
+        const T ex_p = zup ? __ldg(x + c + plane) : T(0);
+        const T ey_p = zup ? __ldg(x + n + c + plane) : T(0);
+        const T ez = __ldg(x + 2 * n + c);
+        const T hx = __ldg(x + 3 * n + c), hy = __ldg(x + 4 * n + c), hz = __ldg(x + 5 * n + c);
+        const T ey_ip = xup ? __ldg(x + n + c + 1) : T(0);
+        const T ez_ip = xup ? __ldg(x + 2 * n + c + 1) : T(0);
+        const T ex_jp = yup ? __ldg(x + c + pitch) : T(0);
+        const T ez_jp = yup ? __ldg(x + 2 * n + c + pitch) : T(0);
+        const T hy_im = (kNeedCh && xdn) ? __ldg(x + 4 * n + c - 1) : T(0);
+        const T hz_im = (kNeedCh && xdn) ? __ldg(x + 5 * n + c - 1) : T(0);
+        const T hx_jm = (kNeedCh && ydn) ? __ldg(x + 3 * n + c - pitch) : T(0);
+        const T hz_jm = (kNeedCh && ydn) ? __ldg(x + 5 * n + c - pitch) : T(0);
         // (C e) on the faces with lowest corner (i, j, k): circulation, (a, b, c) cyclic
         const T cex = (ey_0 + ez_jp) - (ey_p + ez);
         const T cey = (ez + ex_p) - (ez_ip + ex_0);
@@ -88,12 +92,12 @@ __global__ void __launch_bounds__(kEx * kEy) expo_kernel(const ExpoArgs<T> a) {
         const T chx = (hz - hz_jm) - (hy - hy_m);
         const T chy = (hx - hx_m) - (hz - hz_im);
         const T chz = (hy - hy_im) - (hx - hx_jm);
-        const T ch0 = MUARR ? a.ch[c] : chs0;
-        const T ch1 = MUARR ? a.ch[n + c] : chs1;
-        const T ch2 = MUARR ? a.ch[2 * n + c] : chs2;
-        const T y0 = kNeedCh ? kap * (a.cb[c] * chx) : T(0);
-        const T y1 = kNeedCh ? kap * (a.cb[n + c] * chy) : T(0);
-        const T y2 = kNeedCh ? kap * (a.cb[2 * n + c] * chz) : T(0);
+        const T ch0 = MUARR ? __ldg(chp + c) : chs0;
+        const T ch1 = MUARR ? __ldg(chp + n + c) : chs1;
+        const T ch2 = MUARR ? __ldg(chp + 2 * n + c) : chs2;
+        const T y0 = kNeedCh ? kap * (__ldg(cb + c) * chx) : T(0);
+        const T y1 = kNeedCh ? kap * (__ldg(cb + n + c) * chy) : T(0);
+        const T y2 = kNeedCh ? kap * (__ldg(cb + 2 * n + c) * chz) : T(0);
         const T y3 = -kap * (ch0 * cex);
         const T y4 = -kap * (ch1 * cey);
         const T y5 = -kap * (ch2 * cez);
