@@ -750,8 +750,8 @@ int expo_members(fit_grid *g, double dt, const ExpoParams &X, const std::vector<
     for (int p = 0; p < a.nprb; ++p) a.prb[p] = {prb[p].axis, prb[p].i, prb[p].j, prb[p].k};
     // z chunks: enough blocks to fill the GPU with the fewest members of a launch
     const long long cols = (long long)((g->nx + 31) / 32) * ((g->ny + 7) / 8);
-    a.kz = 32;
-    while (a.kz > 4 && cols * ((g->nz + a.kz - 1) / a.kz) < 8 * 152) a.kz /= 2;
+    a.kz = 8;   // measured best on 256^3 (FP32: 8 planes 0.63 of HBM, 32 planes 0.53)
+    while (a.kz > 2 && cols * ((g->nz + a.kz - 1) / a.kz) < 8 * 152) a.kz /= 2;
     if (opts && opts->tile_z > 0) a.kz = std::min(opts->tile_z, g->nz);
     a.nchunk = (g->nz + a.kz - 1) / a.kz;
     if ((long long)a.nchunk * nmem > 65535) return FIT_ERR_UNSUPPORTED;
