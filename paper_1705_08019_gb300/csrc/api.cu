@@ -724,6 +724,7 @@ int expo_members(fit_grid *g, double dt, const ExpoParams &X, const std::vector<
         mem[r].R = P + n6;
         mem[r].Y = P + 2 * n6;
         mem[r].nsub = (int)nsub[t];
+        mem[r].blk = 3 * t;
         mem[r].fin = (const double *)(dt_base + o_fin) + (size_t)r * J * 4;
         mem[r].basis = probes ? (double *)g->xbasis.p + boff[t] : nullptr;
         bp[r] = mem[r].basis;
@@ -746,6 +747,8 @@ int expo_members(fit_grid *g, double dt, const ExpoParams &X, const std::vector<
     a.reg = (const double *)(dt_base + o_reg);
     a.sync = dt / (2.0 * cfl_of(g));
     a.m1 = m1;
+    if ((rc = ensure(g->err, sizeof(int)))) return rc;
+    a.err = (int *)g->err.p;
     a.nprb = probes ? nprb : 0;
     for (int p = 0; p < a.nprb; ++p) a.prb[p] = {prb[p].axis, prb[p].i, prb[p].j, prb[p].k};
     // z chunks: enough blocks to fill the GPU with the fewest members of a launch
@@ -756,6 +759,24 @@ int expo_members(fit_grid *g, double dt, const ExpoParams &X, const std::vector<
     a.nchunk = (g->nz + a.kz - 1) / a.kz;
     if ((long long)a.nchunk * nmem > 65535) return FIT_ERR_UNSUPPORTED;
 
+    // fused pairs (TMA ring) unless the plain kernels are asked for
+    bool fused = !(opts && opts->kernel == 1);
+    TmaMaps maps;
+    CUtensorMap cbmap;
+    ExpoArgs<T> af;
+    if (fused) {
+        const int ftx = expo_pair_tile_x((int)sizeof(T)), fty = expo_pair_tile_y((int)sizeof(T));
+        fused = encode_tma_maps(&maps, (int)sizeof(T), g->nx, g->ny, g->nz, g->pitch, g->xblocks.p, 3 * nmem,
+                                g->coef.p, 3, ftx, fty) &&
+                encode_window_map(&cbmap, (int)sizeof(T), g->nx, g->ny, g->nz, g->pitch, g->coef.p, 3, ftx + 8,
+                                  fty + 2, 3);
+        af = a;
+        const long long fcols = (long long)((g->nx + ftx - 1) / ftx) * ((g->ny + fty - 1) / fty);
+        af.kz = (opts && opts->tile_z > 0) ? std::min(opts->tile_z, g->nz) : 64;
+        while (af.kz > 4 && fcols * ((g->nz + af.kz - 1) / af.kz) < 4 * 152) af.kz /= 2;
+        af.nchunk = (g->nz + af.kz - 1) / af.kz;
+    }
+    const int wait_limit = opts ? std::max(0, opts->debug_wait_limit) : 0;
     const double eb = (double)sizeof(T) * (double)ncell;   // bytes of one component
     const double coefc = 3.0 + (g->mu_array ? 3.0 : 0.0);
     long long nev = 0;
@@ -784,6 +805,36 @@ int expo_members(fit_grid *g, double dt, const ExpoParams &X, const std::vector<
         g->stats.expo_launches += 1;
         g->stats.expo_applications += active;
         g->stats.expo_alg_bytes += eb * (fields * active + coefc);
+        return FIT_OK;
+    };
+    // one fused pair j: y = X R_{j-1}, R_j = X y + eta_j^2 R_{j-1} (not after the last), P update
+    auto run_fused = [&](int j, int active) -> int {
+        af.pair = j;
+        af.substep = a.substep;
+        af.nmem = active;
+        af.eta2 = j < J ? eta2[j - 1] : 0.0;
+        const bool last = j == J;
+        if (profile) {
+            while ((long long)g->ev.size() < 2 * (nev + 1)) {
+                cudaEvent_t e;
+                FIT_CHECK(cudaEventCreate(&e));
+                g->ev.push_back(e);
+            }
+            FIT_CHECK(cudaEventRecord(g->ev[2 * nev], s));
+        }
+        FIT_CHECK(launch_expo_pair_tma<T>(af, maps.state, cbmap, last, g->mu_array, wait_limit, s));
+        if (profile) {
+            FIT_CHECK(cudaEventRecord(g->ev[2 * nev + 1], s));
+            ++nev;
+        }
+        g->stats.kernel_launches += 1;
+        g->stats.expo_launches += 1;
+        g->stats.expo_applications += (long long)active * (last ? 1 : 2);
+        g->stats.expo_alg_bytes += eb * ((last ? 18.0 : 24.0) * active + coefc);
+        if (probes) {
+            FIT_CHECK(launch_expo_gather_fused<T>(af, s));
+            g->stats.kernel_launches += 1;
+        }
         return FIT_OK;
     };
     auto gather = [&](int mode, int active) -> int {
@@ -819,6 +870,10 @@ int expo_members(fit_grid *g, double dt, const ExpoParams &X, const std::vector<
         if ((rc = run(kExpoInit, active)) || (rc = gather(kExpoInit, active))) return rc;
         for (int j = 1; j <= J; ++j) {
             a.pair = j;
+            if (fused) {
+                if ((rc = run_fused(j, active))) return rc;
+                continue;
+            }
             if ((rc = run(kExpoPair1, active)) || (rc = gather(kExpoPair1, active))) return rc;
             if (j < J) {
                 a.eta2 = eta2[j - 1];

@@ -195,6 +195,7 @@ struct ExpoMember {
     T *R;                // R_{j-1}(X) b
     T *Y;                // X R_{j-1}(X) b
     int nsub;            // substeps of this member
+    int blk;             // block index of P in the member blocks (R = blk+1, Y = blk+2) for tensor maps
     const double *fin;   // final substep: [J][4] = alpha_e, gamma_e, alpha_h, gamma_h
     double *basis;       // probe basis: [substep][m+1][nprb] (e at the probe edges)
 };
@@ -218,6 +219,7 @@ struct ExpoArgs {
     double eta2;            // eta_j^2 (second pair launch)
     double sync;            // dt/(2 dt_CFL): half magnetic step in units of X
     int m1;                 // m + 1 (probe basis rows per substep)
+    int *err;               // device error word (bounded waits of the TMA pair kernel)
     int nprb;
     EdgeRef prb[kMaxPrb];
 };
@@ -232,6 +234,21 @@ cudaError_t launch_expo_gather(const ExpoArgs<T> &a, cudaStream_t s);
 cudaError_t launch_expo_dense(int nmem, const double *const *basis, const long long *nrem, const long long *row0,
                               long long max_rows, int q, int m1, int nprb, const double *D, double *out,
                               long long ostride, cudaStream_t s);
+// expo_tma.cu: fused pair (y = X r, r' = X y + eta^2 r, p += alpha r + gamma y) with a TMA ring.
+// Odd pairs read R and write Y, even pairs the reverse; tm_r covers the member blocks with the
+// leapfrog state box (TX+8, TY+2, 1, 3, 1), tm_cb the cb array with the box (TX+8, TY+2, 1, 3).
+template <typename T>
+cudaError_t launch_expo_pair_tma(const ExpoArgs<T> &a, const CUtensorMap &tm_r, const CUtensorMap &tm_cb,
+                                 bool last, bool mu_array, int wait_limit, cudaStream_t s);
+// probe rows 2j-1 (r) and 2j (y = X r, computed at the probe edges) of a fused pair
+template <typename T>
+cudaError_t launch_expo_gather_fused(const ExpoArgs<T> &a, cudaStream_t s);
+int expo_pair_tile_x(int elem_bytes);
+int expo_pair_tile_y(int elem_bytes);
+// a 4-D (x, y, z, component) map over `ncomp` pitched components with an arbitrary box
+bool encode_window_map(CUtensorMap *out, int elem_bytes, int nx, int ny, int nz, int pitch, const void *ptr,
+                       int ncomp, int box_x, int box_y, int box_c);
+
 // out[t] += sum_m pm[m*stride + t], members in order
 cudaError_t add_members(int nmem, long long len, const double *pm, long long stride, double *out, cudaStream_t s);
 

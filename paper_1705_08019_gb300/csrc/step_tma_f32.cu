@@ -87,6 +87,22 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
 }
 }  // namespace
 
+bool encode_window_map(CUtensorMap *out, int eb, int nx, int ny, int nz, int pitch, const void *ptr, int ncomp,
+                       int box_x, int box_y, int box_c) {
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encoder();
+    if (!fn) return false;
+    const CUtensorMapDataType dt = eb == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    const cuuint64_t row = (cuuint64_t)pitch * eb;
+    const cuuint64_t plane = row * ny;
+    cuuint64_t dim[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)ncomp};
+    cuuint64_t str[3] = {row, plane, plane * nz};
+    cuuint32_t box[4] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1, (cuuint32_t)box_c};
+    cuuint32_t ones[4] = {1, 1, 1, 1};
+    return fn(out, dt, 4, const_cast<void *>(ptr), dim, str, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
 bool encode_tma_maps(TmaMaps *out, int eb, int nx, int ny, int nz, int pitch, void *state, int nblocks,
                      const void *coef, int ncoef, int tx, int ty, int nstate) {
     PFN_cuTensorMapEncodeTiled_v12000 fn = encoder();

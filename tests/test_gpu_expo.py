@@ -146,3 +146,26 @@ def test_expo_rejects_unsupported_requests():
     with pytest.raises(fitgb.FitError):
         g.expo_propagate(dt, 5, *W.random_state(w.dims), kind="leja", q=3, m=7)   # odd degree
     g.close()
+
+
+@pytest.mark.parametrize("precision,mu", [(64, False), (64, True), (32, False)])
+def test_fused_pair_kernel_equals_plain_kernels(precision, mu):
+    """The TMA pair kernel (default) and the two plain operator launches per
+    pair (opts.kernel = 1) evaluate the same recurrence: FP64 agrees to
+    rounding, FP32 to a few float ulps of the largest terms."""
+    w, g64, og, dt, dtc = grid_pair(dims=(45, 21, 70), mu=mu, seed=21)
+    g64.close()
+    g = fitgb.Grid(w.dims, w.spacing, w.eps_r, w.mu_r, None, precision)
+    e0, h0 = W.random_state(w.dims, seed=3)
+    out = []
+    for kernel in (0, 1):
+        e = np.array(e0, dtype=g.dtype)
+        h = np.array(h0, dtype=g.dtype)
+        pr = np.zeros((100, len(w.probes)))
+        opts = fitgb.make_opts(homogeneous="leja", expo_substep=12, expo_degree=24, kernel=kernel)
+        fitgb.fit_expo_propagate(g.handle, dt, 100, w.probes, pr, e, h, opts)
+        out.append((pr, e, h))
+    g.close()
+    tol = 1e-12 if precision == 64 else 2e-5
+    (p1, e1, h1), (p2, e2, h2) = out
+    assert probe_relerr(p1, p2) <= tol and relerr(e1, e2) <= tol and relerr(h1, h2) <= tol
