@@ -759,8 +759,10 @@ int expo_members(fit_grid *g, double dt, const ExpoParams &X, const std::vector<
     a.nchunk = (g->nz + a.kz - 1) / a.kz;
     if ((long long)a.nchunk * nmem > 65535) return FIT_ERR_UNSUPPORTED;
 
-    // fused pairs (TMA ring) unless the plain kernels are asked for
-    bool fused = !(opts && opts->kernel == 1);
+    // FP32: fused pairs (TMA ring) unless opts->kernel = 1 asks for the plain launches.  FP64 is
+    // bound by the FP64 pipes, where the plain launches measured faster (12.5 against 10.4
+    // Gcell-applications/s on 256^3); opts->kernel = 2 selects the fused kernel there.
+    bool fused = sizeof(T) == 4 ? !(opts && opts->kernel == 1) : (opts && opts->kernel == 2);
     TmaMaps maps;
     CUtensorMap cbmap;
     ExpoArgs<T> af;
@@ -772,7 +774,7 @@ int expo_members(fit_grid *g, double dt, const ExpoParams &X, const std::vector<
                                   fty + 2, 3);
         af = a;
         const long long fcols = (long long)((g->nx + ftx - 1) / ftx) * ((g->ny + fty - 1) / fty);
-        af.kz = (opts && opts->tile_z > 0) ? std::min(opts->tile_z, g->nz) : 64;
+        af.kz = (opts && opts->tile_z > 0) ? std::min(opts->tile_z, g->nz) : 16;   // 16 measured best (256^3)
         while (af.kz > 4 && fcols * ((g->nz + af.kz - 1) / af.kz) < 4 * 152) af.kz /= 2;
         af.nchunk = (g->nz + af.kz - 1) / af.kz;
     }

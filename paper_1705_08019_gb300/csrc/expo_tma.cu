@@ -17,8 +17,10 @@
 //       row (cb of the halo cells comes with the window),
 //   (c) finishes plane k: r'_e from y_h of planes k and k-1, r'_h from y_e of
 //       planes k and k+1, and the p update.
-// y_h and y_e live in two-plane shared rings.  The first iteration (plane
-// k0-1, zeros below the grid) only primes them.  Waits are bounded as in the
+// The plane-k values of y_h and y_e sit in shared memory; y_h of plane k-1
+// and y_e of plane k+1 are needed only at the thread's own cell and stay in
+// registers (y_e of plane k+1 is stored at the start of the next iteration).
+// The first iteration (plane k0-1, zeros below the grid) only primes them.  Waits are bounded as in the
 // leapfrog kernel: on timeout the CTA records kErrTimeout, waits (bounded)
 // for its own copies and returns.
 #include "internal.h"
@@ -49,12 +51,12 @@ struct PairGeom {
 template <typename T, int TX, int TY, int S>
 struct PairSmem {
     uint64_t bar[S];
-    T yh[2][3][TY + 1][TX + 1];   // y_h, planes k-1 and k; index 0 = low halo
-    T ye[2][3][TY + 1][TX + 1];   // y_e, planes k and k+1; index TY / TX = high halo
+    T yh[3][TY + 1][TX + 1];   // y_h of plane k; index 0 = low halo
+    T ye[3][TY + 1][TX + 1];   // y_e of plane k; index TY / TX = high halo
 };
 
 template <typename T, int TX, int TY, int S, bool LAST, bool MUARR>
-__global__ void __launch_bounds__(TX *TY) expo_pair_tma_kernel(const __grid_constant__ ExpoArgs<T> a,
+__global__ void __launch_bounds__(TX *TY, 4) expo_pair_tma_kernel(const __grid_constant__ ExpoArgs<T> a,
                                                                const __grid_constant__ CUtensorMap tm_r,
                                                                const __grid_constant__ CUtensorMap tm_cb,
                                                                int tiles_x, int tiles_y, int wait_limit) {
@@ -133,6 +135,9 @@ __global__ void __launch_bounds__(TX *TY) expo_pair_tma_kernel(const __grid_cons
     // halo roles: y_h low column / row, y_e high column / row
     const bool lo_col = tid < TY, lo_row = tid >= TY && tid < TY + TX;
     const bool hi_col = tid >= TY + TX && tid < 2 * TY + TX, hi_row = tid >= 2 * TY + TX && tid < 2 * TY + 2 * TX;
+    // carried along z: y_h of plane k-1 (x, y) and y_e of plane k+1 at this cell, and the
+    // two y_e components of this thread's high-halo cell
+    T yhp_x = T(0), yhp_y = T(0), ye_n0 = T(0), ye_n1 = T(0), ye_n2 = T(0), pend_a = T(0), pend_b = T(0);
 
 #define RV(buf, comp, y, x) (buf)[((comp) * EY + (y)) * BX + (x)]
     for (int k = kstart; k < k1; ++k) {
@@ -147,9 +152,21 @@ __global__ void __launch_bounds__(TX *TY) expo_pair_tma_kernel(const __grid_cons
             if (wait_plane(p + 1)) waited = p + 2;
             else bad = 1;
         }
-        const int cur = (k + 2) & 1, nxt = (k + 3) & 1;   // ring slots of planes k and k+1 (k >= -1)
         const int sx = lx + 4, sy = ly + 1;
         const long long c = ((long long)k * ny + j) * pitch + i;
+        // y_e of plane k, computed in the previous iteration, into the shared plane
+        sm.ye[0][ly][lx] = ye_n0;
+        sm.ye[1][ly][lx] = ye_n1;
+        sm.ye[2][ly][lx] = ye_n2;
+        if (hi_col) {
+            const int t = tid - TY - TX;
+            sm.ye[1][t][TX] = pend_a;
+            sm.ye[2][t][TX] = pend_b;
+        } else if (hi_row) {
+            const int t = tid - 2 * TY - TX;
+            sm.ye[0][TY][t] = pend_a;
+            sm.ye[2][TY][t] = pend_b;
+        }
         // p of plane k: issue the loads early, used after the barrier
         T p0 = T(0), p1 = T(0), p2 = T(0), p3 = T(0), p4 = T(0), p5 = T(0);
         if (k >= k0 && own) {
@@ -171,25 +188,27 @@ __global__ void __launch_bounds__(TX *TY) expo_pair_tma_kernel(const __grid_cons
             if (ci < 0 || cj < 0 || ci >= nx || cj >= ny || k < 0) return T(0);
             return __ldg(chp + comp * n + ((long long)k * ny + cj) * pitch + ci);
         };
+        T yhx, yhy, yhz;   // y_h of plane k at this cell
+        yh_at(sx, sy, ch_at(i, j, 0), ch_at(i, j, 1), ch_at(i, j, 2), yhx, yhy, yhz);
+        sm.yh[0][ly + 1][lx + 1] = yhx;
+        sm.yh[1][ly + 1][lx + 1] = yhy;
+        sm.yh[2][ly + 1][lx + 1] = yhz;
         {
             T o0, o1, o2;
-            yh_at(sx, sy, ch_at(i, j, 0), ch_at(i, j, 1), ch_at(i, j, 2), o0, o1, o2);
-            sm.yh[cur][0][ly + 1][lx + 1] = o0;
-            sm.yh[cur][1][ly + 1][lx + 1] = o1;
-            sm.yh[cur][2][ly + 1][lx + 1] = o2;
             if (lo_col) {   // cell (i0-1, j0+tid): y_h y and z
                 const int y = tid + 1;
                 yh_at(3, y, T(0), ch_at(i0 - 1, j0 + tid, 1), ch_at(i0 - 1, j0 + tid, 2), o0, o1, o2);
-                sm.yh[cur][1][y][0] = o1;
-                sm.yh[cur][2][y][0] = o2;
+                sm.yh[1][y][0] = o1;
+                sm.yh[2][y][0] = o2;
             } else if (lo_row) {   // cell (i0+t, j0-1): y_h x and z
                 const int t = tid - TY;
                 yh_at(t + 4, 0, ch_at(i0 + t, j0 - 1, 0), T(0), ch_at(i0 + t, j0 - 1, 2), o0, o1, o2);
-                sm.yh[cur][0][0][t + 1] = o0;
-                sm.yh[cur][2][0][t + 1] = o2;
+                sm.yh[0][0][t + 1] = o0;
+                sm.yh[2][0][t + 1] = o2;
             }
         }
-        // (b) y_e of plane k+1 at (x, y): kap cb (C~ r_h), r_h of planes k+1 and k
+        // (b) y_e of plane k+1 at (x, y): kap cb (C~ r_h), r_h of planes k+1 and k; kept in
+        // registers until the next iteration stores it
         auto ye_at = [&](int x, int y, T &o0, T &o1, T &o2) {
             const T hx = RV(hN, 0, y, x), hy = RV(hN, 1, y, x), hz = RV(hN, 2, y, x);
             const T tx = (hz - RV(hN, 2, y - 1, x)) - (hy - RV(hC, 1, y, x));
@@ -199,22 +218,20 @@ __global__ void __launch_bounds__(TX *TY) expo_pair_tma_kernel(const __grid_cons
             o1 = kap * (RV(bN, 1, y, x) * ty);
             o2 = kap * (RV(bN, 2, y, x) * tz);
         };
+        const T yex = ye_n0, yey = ye_n1, yez = ye_n2;   // y_e of plane k at this cell
+        ye_at(sx, sy, ye_n0, ye_n1, ye_n2);
         {
             T o0, o1, o2;
-            ye_at(sx, sy, o0, o1, o2);
-            sm.ye[nxt][0][ly][lx] = o0;
-            sm.ye[nxt][1][ly][lx] = o1;
-            sm.ye[nxt][2][ly][lx] = o2;
             if (hi_col) {   // cell (i0+TX, j0+t): y_e y and z
                 const int t = tid - TY - TX;
                 ye_at(TX + 4, t + 1, o0, o1, o2);
-                sm.ye[nxt][1][t][TX] = o1;
-                sm.ye[nxt][2][t][TX] = o2;
+                pend_a = o1;
+                pend_b = o2;
             } else if (hi_row) {   // cell (i0+t, j0+TY): y_e x and z
                 const int t = tid - 2 * TY - TX;
                 ye_at(t + 4, TY + 1, o0, o1, o2);
-                sm.ye[nxt][0][TY][t] = o0;
-                sm.ye[nxt][2][TY][t] = o2;
+                pend_a = o0;
+                pend_b = o2;
             }
         }
         if (__syncthreads_or(bad)) {
@@ -223,18 +240,14 @@ __global__ void __launch_bounds__(TX *TY) expo_pair_tma_kernel(const __grid_cons
         }
         // (c) finish plane k
         if (k >= k0 && own) {
-            const int pv = cur ^ 1;   // slot of plane k-1 (y_h) and of plane k+1 (y_e)
-            const T yhx = sm.yh[cur][0][ly + 1][lx + 1], yhy = sm.yh[cur][1][ly + 1][lx + 1],
-                    yhz = sm.yh[cur][2][ly + 1][lx + 1];
-            const T yex = sm.ye[cur][0][ly][lx], yey = sm.ye[cur][1][ly][lx], yez = sm.ye[cur][2][ly][lx];
-            // r'_e = kap cb C~ y_h + eta^2 r_e
-            const T tx = (yhz - sm.yh[cur][2][ly][lx + 1]) - (yhy - sm.yh[pv][1][ly + 1][lx + 1]);
-            const T ty = (yhx - sm.yh[pv][0][ly + 1][lx + 1]) - (yhz - sm.yh[cur][2][ly + 1][lx]);
-            const T tz = (yhy - sm.yh[cur][1][ly + 1][lx]) - (yhx - sm.yh[cur][0][ly][lx + 1]);
-            // r'_h = -kap ch C y_e + eta^2 r_h
-            const T cx = (yey + sm.ye[cur][2][ly + 1][lx]) - (sm.ye[pv][1][ly][lx] + yez);
-            const T cy = (yez + sm.ye[pv][0][ly][lx]) - (sm.ye[cur][2][ly][lx + 1] + yex);
-            const T cz = (yex + sm.ye[cur][1][ly][lx + 1]) - (sm.ye[cur][0][ly + 1][lx] + yey);
+            // r'_e = kap cb C~ y_h + eta^2 r_e (y_h of plane k-1 from registers)
+            const T tx = (yhz - sm.yh[2][ly][lx + 1]) - (yhy - yhp_y);
+            const T ty = (yhx - yhp_x) - (yhz - sm.yh[2][ly + 1][lx]);
+            const T tz = (yhy - sm.yh[1][ly + 1][lx]) - (yhx - sm.yh[0][ly][lx + 1]);
+            // r'_h = -kap ch C y_e + eta^2 r_h (y_e of plane k+1 from registers)
+            const T cx = (yey + sm.ye[2][ly + 1][lx]) - (ye_n1 + yez);
+            const T cy = (yez + ye_n0) - (sm.ye[2][ly][lx + 1] + yex);
+            const T cz = (yex + sm.ye[1][ly][lx + 1]) - (sm.ye[0][ly + 1][lx] + yey);
             const T rex = RV(eC, 0, sy, sx), rey = RV(eC, 1, sy, sx), rez = RV(eC, 2, sy, sx);
             const T rhx = RV(hC, 0, sy, sx), rhy = RV(hC, 1, sy, sx), rhz = RV(hC, 2, sy, sx);
             if (!LAST) {
@@ -252,7 +265,9 @@ __global__ void __launch_bounds__(TX *TY) expo_pair_tma_kernel(const __grid_cons
             P[4 * n + c] = p4 + (al_h * rhy + ga_h * yhy);
             P[5 * n + c] = p5 + (al_h * rhz + ga_h * yhz);
         }
-        __syncthreads();   // stage p and the y slots of plane k-1 / k are free again
+        yhp_x = yhx;
+        yhp_y = yhy;
+        __syncthreads();   // stage p and the shared y planes are free again
         if (tid == 0 && issued < total) {
             proxy_fence();
             issue(issued);

@@ -150,15 +150,16 @@ def test_expo_rejects_unsupported_requests():
 
 @pytest.mark.parametrize("precision,mu", [(64, False), (64, True), (32, False)])
 def test_fused_pair_kernel_equals_plain_kernels(precision, mu):
-    """The TMA pair kernel (default) and the two plain operator launches per
-    pair (opts.kernel = 1) evaluate the same recurrence: FP64 agrees to
-    rounding, FP32 to a few float ulps of the largest terms."""
+    """The TMA pair kernel (opts.kernel = 2; the FP32 default) and the two
+    plain operator launches per pair (opts.kernel = 1; the FP64 default)
+    evaluate the same recurrence: FP64 agrees to rounding, FP32 to a few
+    float ulps of the largest terms."""
     w, g64, og, dt, dtc = grid_pair(dims=(45, 21, 70), mu=mu, seed=21)
     g64.close()
     g = fitgb.Grid(w.dims, w.spacing, w.eps_r, w.mu_r, None, precision)
     e0, h0 = W.random_state(w.dims, seed=3)
     out = []
-    for kernel in (0, 1):
+    for kernel in (2, 1):
         e = np.array(e0, dtype=g.dtype)
         h = np.array(h0, dtype=g.dtype)
         pr = np.zeros((100, len(w.probes)))
