@@ -181,6 +181,27 @@ int fit_grid_create(int nx, int ny, int nz, double dx, double dy, double dz,
                     const float *eps_r, const float *mu_r, const float *sigma,
                     int precision, unsigned flags, fit_grid **out);
 
+/* A graded (tensor-product) grid: cell (i,j,k) measures dx[i] x dy[j] x dz[k]
+ * (host arrays of nx, ny, nz sizes [m]); everything else as fit_grid_create.
+ * Material matrices with the local sizes (Sec. II, eq. maxwell_grid3):
+ *   M_eps(edge along a at q) = eps0 / d_a[q_a] * sum over the four cells
+ *     around the edge of eps_r * d_b * d_c / 4 (each cell's part of the dual
+ *     facet); M_sigma likewise;
+ *   M_mu(face normal to a at q) = mu0 d_b[q_b] d_c[q_c] / s,
+ *     s = (d_a[q_a-1]/2)/mu_r(q-u_a) + (d_a[q_a]/2)/mu_r(q).
+ * fit_cfl_dt returns eq. (cfl) with each cell's own sizes.  The exponential
+ * propagators interpolate on i[-beta, beta] with beta = ||A||_1 (the largest
+ * absolute row sum of A, a bound on ||A||_2), since eq. (cfl) is only an
+ * estimate on such grids.  fit_adjoint_grad returns FIT_ERR_UNSUPPORTED. */
+int fit_grid_create_graded(int nx, int ny, int nz, const double *dx, const double *dy, const double *dz,
+                           const float *eps_r, const float *mu_r, const float *sigma,
+                           int precision, unsigned flags, fit_grid **out);
+
+/* The bound beta >= ||A||_2 of the grid's skew system matrix that the
+ * exponential propagators use: 2/dt_CFL on a uniform grid (the bound eq. (cfl)
+ * is derived from), ||A||_1 on a graded one. */
+int fit_spectral_bound(const fit_grid *g, double *beta);
+
 /* Free the grid and every workspace it owns, after the device has finished
  * all work (cudaDeviceSynchronize).  NULL is accepted. */
 void fit_grid_destroy(fit_grid *g);
@@ -244,8 +265,9 @@ int paraexp_run(fit_grid *g, double dt, int K, const long *win,
 /* Exponential propagators (Sec. III-B, "Approximation of the matrix
  * exponential").  On a lossless grid the transformed system of eq.
  * (FIT_ode_2) has the skew matrix A, whose spectrum lies in i[-beta, beta],
- * beta = ||A||_2 <= 2/dt_CFL (the bound behind eq. (cfl)).  With
- * X = dt_CFL A, a substep of q leapfrog steps is exp(c X), c = q dt/dt_CFL,
+ * beta = ||A||_2 <= fit_spectral_bound (2/dt_CFL on uniform grids, the
+ * bound behind eq. (cfl)).  With X = (2/beta) A, a substep of q leapfrog
+ * steps is exp(c X), c = q dt beta/2 (= q dt/dt_CFL on uniform grids),
  * replaced by the Newton interpolant p_m of exp(c z) at m+1 points of
  * i[-2, 2]:
  *   Leja:   xi_0 = 0, then conjugate pairs +-i eta_j, eta_j the first
@@ -258,17 +280,17 @@ int paraexp_run(fit_grid *g, double dt, int K, const long *win,
  * alpha_j = d_{2j-1} - i eta_j d_{2j} and gamma_j = d_{2j}, d_k the divided
  * differences (both real for conjugate points).  Since polynomials of A and
  * of M^{-1}K are similar, the library applies X in the untransformed
- * voltages: X (e, h) = (dt_CFL/dt) (cb C~h, -ch C e) on a lossless grid.
+ * voltages: X (e, h) = (2/(beta dt)) (cb C~h, -ch C e) on a lossless grid.
  *
  * fit_expo_plan: the substep q (leapfrog steps) and degree m for
- * dt_ratio = dt/dt_CFL, the tolerance eps_A and the field precision
+ * dt_ratio = dt beta/2, the tolerance eps_A and the field precision
  * (32, 64).  The condition ||Delta A|| <= eps_A ||A|| of Sec. III-D, with
  * ||A|| replaced by beta, holds for a normal A when
  *   max_{z in i[-2,2]} |log(p_m(z) e^{-cz})| + u_p H_m <= 2 c eps_A,
  * evaluated at z = i 2l/4096 (l = 0..4096); H_m = max_z sum_k |d_k w_k(z)|
  * bounds the rounding of the Newton sum (u_p: unit roundoff of the
  * precision); the same must hold with tau c for every output fraction
- * tau = i/q.  Over q with q dt/dt_CFL <= 32 and even m <= 120 the least m/q
+ * tau = i/q.  Over q with q dt beta/2 <= 32 and even m <= 120 the least m/q
  * wins (ties: smaller q).  Host only (no device work); FIT_ERR_ARG if no
  * pair meets the tolerance. */
 int fit_expo_plan(int kind, double dt_ratio, double tol, int precision, int *substep, int *degree);

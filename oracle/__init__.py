@@ -11,7 +11,8 @@ array over the (nx+1)(ny+1)(nz+1) primal points, x fastest; numpy shape
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests
 (dense brute force, Yee dispersion eigenvalues, energy balance, Gauss law,
-mirror/rotation symmetry, ParaExp linearity, finite differences).
+mirror/rotation symmetry, ParaExp linearity, finite differences; graded
+grids: uniform limit, exact energy of uniform fields, eigenvalue bounds).
 """
 from __future__ import annotations
 
@@ -78,6 +79,12 @@ def _load():
         lib.oracle_paraexp.argtypes = [ctypes.POINTER(_Grid), I, P, P, I, P, I, P, P, P, P, P]
         lib.oracle_adjoint.restype = I
         lib.oracle_adjoint.argtypes = [ctypes.POINTER(_Grid), P, P, I, L, L, P, I, P, I, P, P]
+        lib.oracle_cfl_dt_graded.restype = D
+        lib.oracle_cfl_dt_graded.argtypes = [I, I, I, P, P, P, P, P]
+        lib.oracle_coeffs_graded.restype = I
+        lib.oracle_coeffs_graded.argtypes = [I, I, I, P, P, P, P, P, P, D, I, I, P, P, P, P, P, P]
+        lib.oracle_A_rowsum.restype = D
+        lib.oracle_A_rowsum.argtypes = [ctypes.POINTER(_Grid), P, P]
         lib.oracle_apply_A.restype = I
         lib.oracle_apply_A.argtypes = [ctypes.POINTER(_Grid), P, P, P, P]
         lib.oracle_constants.restype = None
@@ -110,11 +117,28 @@ def waveform(kind, amp, f0, width, delay, t):
     return _load().oracle_waveform(int(kind), float(amp), float(f0), float(width), float(delay), float(t))
 
 
+def graded_spacing(dims, spacing):
+    """Per-axis cell sizes (three float64 arrays) if `spacing` holds any
+    array, else None (a uniform grid)."""
+    if all(np.ndim(v) == 0 for v in spacing):
+        return None
+    out = []
+    for n, v in zip(dims, spacing):
+        a = np.full(int(n), float(v)) if np.ndim(v) == 0 else np.ascontiguousarray(v, dtype=np.float64)
+        if a.shape != (int(n),):
+            raise ValueError("a graded spacing needs one size per cell along its axis")
+        out.append(a)
+    return out
+
+
 def cfl_dt(dims, spacing, eps_r, mu_r=None):
-    """Eq. (cfl): the largest stable step estimate."""
+    """Eq. (cfl): the largest stable step estimate (per-cell sizes on a graded grid)."""
     nx, ny, nz = dims
     e = _f32(eps_r, (nz, ny, nx))
     m = _f32(mu_r, (nz, ny, nx))
+    gs = graded_spacing(dims, spacing)
+    if gs is not None:
+        return _load().oracle_cfl_dt_graded(nx, ny, nz, *(_ptr(a) for a in gs), _ptr(e), _ptr(m))
     return _load().oracle_cfl_dt(nx, ny, nz, *map(float, spacing), _ptr(e), _ptr(m))
 
 
@@ -143,7 +167,9 @@ class OracleGrid:
     def __init__(self, dims, spacing, eps_r, mu_r=None, sigma=None, dt=None,
                  cfl_fraction=0.95, sigma_scheme=0, round32=False, store32=False):
         self.nx, self.ny, self.nz = (int(v) for v in dims)
-        self.spacing = tuple(float(v) for v in spacing)
+        self.graded = graded_spacing(dims, spacing)
+        self.spacing = (tuple(float(np.mean(a)) for a in self.graded) if self.graded is not None
+                        else tuple(float(v) for v in spacing))
         shp = (self.nz, self.ny, self.nx)
         self.eps_r = _f32(eps_r, shp)
         self.mu_r = _f32(mu_r, shp)
@@ -151,17 +177,25 @@ class OracleGrid:
         self.sigma_scheme = int(sigma_scheme)
         self.round32 = bool(round32)
         if dt is None:
-            dt = cfl_fraction * cfl_dt(dims, spacing, self.eps_r, self.mu_r)
+            dt = cfl_fraction * cfl_dt(dims, spacing if self.graded is not None else self.spacing, self.eps_r,
+                                       self.mu_r)
         self.dt = float(dt)
         fshape = (3, self.nz + 1, self.ny + 1, self.nx + 1)
         self.field_shape = fshape
         self.ca, self.cb, self.ch = (np.zeros(fshape) for _ in range(3))
         self.meps, self.msig, self.mmu = (np.zeros(fshape) for _ in range(3))
-        rc = _load().oracle_coeffs(self.nx, self.ny, self.nz, *self.spacing,
-                                   _ptr(self.eps_r), _ptr(self.mu_r), _ptr(self.sigma),
-                                   self.dt, self.sigma_scheme, int(self.round32),
-                                   _ptr(self.ca), _ptr(self.cb), _ptr(self.ch),
-                                   _ptr(self.meps), _ptr(self.msig), _ptr(self.mmu))
+        if self.graded is not None:
+            rc = _load().oracle_coeffs_graded(self.nx, self.ny, self.nz, *(_ptr(a) for a in self.graded),
+                                              _ptr(self.eps_r), _ptr(self.mu_r), _ptr(self.sigma),
+                                              self.dt, self.sigma_scheme, int(self.round32),
+                                              _ptr(self.ca), _ptr(self.cb), _ptr(self.ch),
+                                              _ptr(self.meps), _ptr(self.msig), _ptr(self.mmu))
+        else:
+            rc = _load().oracle_coeffs(self.nx, self.ny, self.nz, *self.spacing,
+                                       _ptr(self.eps_r), _ptr(self.mu_r), _ptr(self.sigma),
+                                       self.dt, self.sigma_scheme, int(self.round32),
+                                       _ptr(self.ca), _ptr(self.cb), _ptr(self.ch),
+                                       _ptr(self.meps), _ptr(self.msig), _ptr(self.mmu))
         if rc:
             raise ValueError(f"oracle_coeffs failed ({rc})")
         self._g = _Grid(self.nx, self.ny, self.nz, (ctypes.c_double * 3)(*self.spacing), self.dt,
@@ -217,8 +251,17 @@ class OracleGrid:
             raise ValueError(f"oracle_apply_A failed ({rc})")
         return oe, oh
 
+    def A_rowsum(self):
+        """max absolute row sum of A (= ||A||_1 = ||A||_inf, a bound on ||A||_2)
+        and the sums per edge and face."""
+        oe, oh = self.zeros(), self.zeros()
+        best = _load().oracle_A_rowsum(ctypes.byref(self._g), _ptr(oe), _ptr(oh))
+        return best, oe, oh
+
     def adjoint(self, nsteps, sources=(), probes=(), step0=0):
         """J = sum_n sum_p (e_p^n/L_p)^2 and dJ/d eps_r per cell (shape (nz, ny, nx))."""
+        if self.graded is not None:
+            raise NotImplementedError("the adjoint oracle covers uniform grids")
         src, prb = _structs(sources, probes)
         J = np.zeros(1)
         g = np.zeros((self.nz, self.ny, self.nx))

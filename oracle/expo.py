@@ -13,10 +13,12 @@ skew matrix A of eq. (FIT_ode_2), applied by ``fit_oracle.c``.
 Readings of the paper (it defers the details to its references):
 
 * Interval.  A is skew, so its eigenvalues lie on i[-beta, beta] with
-  beta = ||A||_2.  beta is bounded by 2/dt_CFL, dt_CFL of eq. (cfl) (the
-  estimate eq. (cfl) comes from), and that bound is used: X = A dt_CFL has
-  its spectrum in i[-2, 2].  A substep of length h_s is exp(c X) with
-  c = h_s / dt_CFL.
+  beta >= ||A||_2.  On a uniform grid beta = 2/dt_CFL, dt_CFL of eq. (cfl)
+  (the Yee bound the estimate comes from); on a graded grid, where eq. (cfl)
+  is only an estimate, beta = ||A||_1, the largest absolute row sum (the norm
+  Higham's parameter selection works with).  X = (2/beta) A has its spectrum
+  in i[-2, 2]; a substep of length h_s is exp(c X) with c = h_s beta/2.  The
+  functions take dt_cfl = 2/beta.
 * Points.  Conjugate Leja points of i[-2, 2]: xi_0 = 0, then for each pair
   the point i*eta, eta in [0, 2], that maximises the product of distances to
   all points chosen so far, followed by its conjugate.  eta runs over the
@@ -241,14 +243,24 @@ def _combine(basis, d):
     return v.real
 
 
+def spectral_bound(og):
+    """beta >= ||A||_2: 2/dt_CFL of eq. (cfl) on a uniform grid (the Yee bound
+    the estimate comes from), the largest absolute row sum of A (||A||_1) on a
+    graded grid, where eq. (cfl) is only an estimate."""
+    from . import cfl_dt
+    if og.graded is None:
+        return 2.0 / cfl_dt((og.nx, og.ny, og.nz), og.spacing, og.eps_r, og.mu_r)
+    return og.A_rowsum()[0]
+
+
 def propagate(og, nsteps, e0, h0, probes=(), kind="leja", q=None, m=None, tol=1e-12, precision=64,
               dt_cfl=None, stagger_h=False):
     """w(t) = exp((t - t0) A) u0 from the synchronised state (e0, h0) at t0,
     in substeps L_{m,c}(q dt A) with dense output at every leapfrog step.
     Returns (probes[n, p] = e at t0 + (n+1) dt, e(T), h(T) or, with
-    stagger_h, h(T - dt/2)), T = t0 + nsteps dt."""
-    from . import cfl_dt
-    dt_cfl = float(dt_cfl) if dt_cfl is not None else cfl_dt((og.nx, og.ny, og.nz), og.spacing, og.eps_r, og.mu_r)
+    stagger_h, h(T - dt/2)), T = t0 + nsteps dt.  dt_cfl is the normalisation
+    2/beta (X = (2/beta) A); by default beta = spectral_bound(og)."""
+    dt_cfl = float(dt_cfl) if dt_cfl is not None else 2.0 / spectral_bound(og)
     u = og.dt / dt_cfl
     if q is None or m is None:
         q, m = plan(kind, u, tol, precision)
@@ -300,11 +312,10 @@ def paraexp(og, K, win, sources=(), probes=(), kind="leja", q=None, m=None, tol=
     propagator above.  The initial value (e0, h0) = (e^{W_0}, h^{W_0-1/2})
     (zero if both are None) gives w_1, synchronised like the v_j.  Returns
     (probes[n, p] for absolute steps win[0]+1..win[K], e(T), h(T - dt/2))."""
-    from . import cfl_dt
     win = [int(v) for v in win]
     nt = win[K] - win[0]
     if dt_cfl is None:
-        dt_cfl = cfl_dt((og.nx, og.ny, og.nz), og.spacing, og.eps_r, og.mu_r)
+        dt_cfl = 2.0 / spectral_bound(og)
     if q is None or m is None:
         q, m = plan(kind, og.dt / dt_cfl, tol, precision)
     pr = np.zeros((nt, len(probes)))

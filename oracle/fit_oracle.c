@@ -603,3 +603,167 @@ int oracle_apply_A(const or_grid *g, const double *ue, const double *uh, double 
     free(te); free(th);
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Graded (tensor-product) grids: cell (i,j,k) has the size             */
+/* dx[i] x dy[j] x dz[k].  Eq. (cfl) takes each cell's own sizes:        */
+/*   dt_CFL = min_j sqrt(eps_j mu_j / (1/dx_j^2 + 1/dy_j^2 + 1/dz_j^2)). */
+/* ------------------------------------------------------------------ */
+double oracle_cfl_dt_graded(int nx, int ny, int nz, const double *dx, const double *dy, const double *dz,
+                            const float *eps_r, const float *mu_r) {
+    double best = -1.0;
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                long c = cidx(nx, ny, i, j, k);
+                double inv = 1.0 / (dx[i] * dx[i]) + 1.0 / (dy[j] * dy[j]) + 1.0 / (dz[k] * dz[k]);
+                double em = OR_EPS0 * (double)eps_r[c] * OR_MU0 * (mu_r ? (double)mu_r[c] : 1.0);
+                double t = sqrt(em / inv);
+                if (best < 0.0 || t < best) best = t;
+            }
+    return best;
+}
+
+/* ------------------------------------------------------------------ */
+/* Material matrices on a graded grid (Sec. II, eq. maxwell_grid3), the   */
+/* same readings as oracle_coeffs with the local sizes:                   */
+/*  - M_eps of the edge along a at q: eps0 / L * sum over the four cells   */
+/*    around it of eps_r * (d_b/2)(d_c/2) (the part of the dual facet     */
+/*    inside each cell), L = d_a[q_a]: the area-weighted mean times the   */
+/*    dual area over the length.  M_sigma likewise.                        */
+/*  - M_mu of the face normal to a at q: mu0 * A / s with A = d_b[q_b]     */
+/*    d_c[q_c] and s = (d_a[q_a-1]/2)/mu_r(q - u_a) + (d_a[q_a]/2)/mu_r(q):*/
+/*    the two halves of the dual edge in series (the length-weighted      */
+/*    harmonic mean of mu_r).                                              */
+/*  - ca, cb, ch as in oracle_coeffs.                                      */
+/* ------------------------------------------------------------------ */
+int oracle_coeffs_graded(int nx, int ny, int nz, const double *dx, const double *dy, const double *dz,
+                         const float *eps_r, const float *mu_r, const float *sigma,
+                         double dt, int sigma_scheme, int round32,
+                         double *ca, double *cb, double *ch,
+                         double *meps, double *msig, double *mmu) {
+    int n[3] = {nx, ny, nz};
+    const double *ds[3] = {dx, dy, dz};
+    long Np = (long)(nx + 1) * (ny + 1) * (nz + 1);
+    if (nx < 1 || ny < 1 || nz < 1 || !(dt > 0.0)) return -1;
+    memset(ca, 0, sizeof(double) * 3 * Np);
+    memset(cb, 0, sizeof(double) * 3 * Np);
+    memset(ch, 0, sizeof(double) * 3 * Np);
+    memset(meps, 0, sizeof(double) * 3 * Np);
+    memset(msig, 0, sizeof(double) * 3 * Np);
+    memset(mmu, 0, sizeof(double) * 3 * Np);
+    for (int a = 0; a < 3; ++a) {
+        int b = (a + 1) % 3, c = (a + 2) % 3;
+        for (int k = 0; k <= nz; ++k)
+            for (int j = 0; j <= ny; ++j)
+                for (int i = 0; i <= nx; ++i) {
+                    int q[3] = {i, j, k};
+                    long p = (long)a * Np + pidx(nx, ny, i, j, k);
+                    if (edge_free(n, a, q)) {
+                        double len = ds[a][q[a]];
+                        double esum = 0.0, ssum = 0.0;
+                        for (int sb = 0; sb < 2; ++sb)
+                            for (int sc = 0; sc < 2; ++sc) {
+                                int r[3] = {q[0], q[1], q[2]};
+                                r[b] -= sb;
+                                r[c] -= sc;
+                                long cc = cidx(nx, ny, r[0], r[1], r[2]);
+                                double w = ds[b][r[b]] * ds[c][r[c]] / 4.0;
+                                esum += (double)eps_r[cc] * w;
+                                ssum += (sigma ? (double)sigma[cc] : 0.0) * w;
+                            }
+                        double Me = OR_EPS0 * esum / len;
+                        double Ms = ssum / len;
+                        double av = dt * Ms / (2.0 * Me);
+                        double vca, vcb;
+                        if (sigma_scheme == 0) {
+                            vca = (1.0 - av) / (1.0 + av);
+                            vcb = dt / (Me * (1.0 + av));
+                        } else {
+                            vca = 1.0 - 2.0 * av;
+                            vcb = dt / Me;
+                        }
+                        if (round32) { vca = (double)(float)vca; vcb = (double)(float)vcb; }
+                        ca[p] = vca;
+                        cb[p] = vcb;
+                        meps[p] = Me;
+                        msig[p] = Ms;
+                    }
+                    if (face_interior(n, a, q)) {
+                        int r[3] = {q[0], q[1], q[2]};
+                        r[a] -= 1;
+                        double m1 = mu_r ? (double)mu_r[cidx(nx, ny, r[0], r[1], r[2])] : 1.0;
+                        double m2 = mu_r ? (double)mu_r[cidx(nx, ny, q[0], q[1], q[2])] : 1.0;
+                        double area = ds[b][q[b]] * ds[c][q[c]];
+                        double s = (ds[a][q[a] - 1] / 2.0) / m1 + (ds[a][q[a]] / 2.0) / m2;
+                        double Mm = OR_MU0 * area / s;
+                        double vch = dt / Mm;
+                        if (round32) vch = (double)(float)vch;
+                        ch[p] = vch;
+                        mmu[p] = Mm;
+                    }
+                }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Absolute row sums of the skew matrix A of eq. (FIT_ode_2), the norm   */
+/* ||A||_1 = ||A||_inf of Higham's parameter selection being their max:  */
+/*   edge e: M_eps(e)^{-1/2} sum_{faces f of e} M_mu(f)^{-1/2}            */
+/*   face f: M_mu(f)^{-1/2} sum_{edges e of f} M_eps(e)^{-1/2}            */
+/* over the degrees of freedom (the incidences of curl_h and curl_e).     */
+/* Returns the maximum; oe, oh (3*Np each, or NULL) receive the sums.     */
+/* ------------------------------------------------------------------ */
+double oracle_A_rowsum(const or_grid *g, double *oe, double *oh) {
+    int nx = g->nx, ny = g->ny, nz = g->nz;
+    int n[3] = {nx, ny, nz};
+    long Np = np_of(g);
+    double *ie = (double *)calloc((size_t)(3 * Np), sizeof(double));
+    double *ih = (double *)calloc((size_t)(3 * Np), sizeof(double));
+    double best = 0.0;
+    if (!ie || !ih) { free(ie); free(ih); return -1.0; }
+    for (int a = 0; a < 3; ++a)
+        for (int k = 0; k <= nz; ++k)
+            for (int j = 0; j <= ny; ++j)
+                for (int i = 0; i <= nx; ++i) {
+                    int q[3] = {i, j, k};
+                    long p = (long)a * Np + pidx(nx, ny, i, j, k);
+                    if (edge_free(n, a, q)) ie[p] = 1.0 / sqrt(g->meps[p]);
+                    if (face_interior(n, a, q)) ih[p] = 1.0 / sqrt(g->mmu[p]);
+                }
+    for (int a = 0; a < 3; ++a) {
+        int b = (a + 1) % 3, c = (a + 2) % 3;
+        for (int k = 0; k <= nz; ++k)
+            for (int j = 0; j <= ny; ++j)
+                for (int i = 0; i <= nx; ++i) {
+                    int q[3] = {i, j, k};
+                    long p = (long)a * Np + pidx(nx, ny, i, j, k);
+                    double se = 0.0, sh = 0.0;
+                    if (edge_free(n, a, q)) {   /* faces h_c(q), h_c(q-u_b), h_b(q), h_b(q-u_c) */
+                        int qb[3] = {q[0], q[1], q[2]}, qc[3] = {q[0], q[1], q[2]};
+                        qb[b] -= 1;
+                        qc[c] -= 1;
+                        double s = ih[(long)c * Np + pidx(nx, ny, q[0], q[1], q[2])] + ih[(long)b * Np + pidx(nx, ny, q[0], q[1], q[2])];
+                        if (qb[b] >= 0) s += ih[(long)c * Np + pidx(nx, ny, qb[0], qb[1], qb[2])];
+                        if (qc[c] >= 0) s += ih[(long)b * Np + pidx(nx, ny, qc[0], qc[1], qc[2])];
+                        se = ie[p] * s;
+                    }
+                    if (face_interior(n, a, q)) {   /* edges e_b(q), e_c(q+u_b), e_b(q+u_c), e_c(q) */
+                        int qb[3] = {q[0], q[1], q[2]}, qc[3] = {q[0], q[1], q[2]};
+                        qb[b] += 1;
+                        qc[c] += 1;
+                        double s = ie[(long)b * Np + pidx(nx, ny, q[0], q[1], q[2])] + ie[(long)c * Np + pidx(nx, ny, q[0], q[1], q[2])];
+                        if (qb[b] <= n[b]) s += ie[(long)c * Np + pidx(nx, ny, qb[0], qb[1], qb[2])];
+                        if (qc[c] <= n[c]) s += ie[(long)b * Np + pidx(nx, ny, qc[0], qc[1], qc[2])];
+                        sh = ih[p] * s;
+                    }
+                    if (oe) oe[p] = se;
+                    if (oh) oh[p] = sh;
+                    if (se > best) best = se;
+                    if (sh > best) best = sh;
+                }
+    }
+    free(ie); free(ih);
+    return best;
+}

@@ -46,6 +46,10 @@ struct fit_grid {
     bool mu_array = false, lossy = false;
     double eps_mu_min = 1.0;
     unsigned flags = 0;
+    // graded grids: per-axis cell sizes on the device, eq. (cfl) with local sizes, ||A||_1
+    bool graded = false;
+    Buf spc;
+    double cfl_graded = 0.0, rowsum = 0.0;
     // coefficient cache
     bool c_valid = false, c_has_energy = false;
     double c_dt = 0.0;
@@ -118,6 +122,7 @@ cudaMemcpyKind kind_from_dev(const void *dst) {
 }
 
 double cfl_of(const fit_grid *g) {
+    if (g->graded) return g->cfl_graded;
     const double inv = 1.0 / (g->d[0] * g->d[0]) + 1.0 / (g->d[1] * g->d[1]) + 1.0 / (g->d[2] * g->d[2]);
     return std::sqrt(kEps0 * kMu0 * (double)g->eps_mu_min / inv);
 }
@@ -152,6 +157,11 @@ int ensure_coeffs(fit_grid *g, double dt, int scheme, bool need_energy, cudaStre
     }
     T *cb = (T *)g->coef.p;
     T *ca = g->lossy ? cb + 3 * g->ncp : nullptr;
+    if (g->graded)
+        FIT_CHECK(build_coeffs_graded<T>(g->nx, g->ny, g->nz, g->pitch, (const double *)g->spc.p, g->eps, g->mu, g->sig,
+                                         dt, scheme, ca, cb, (T *)g->ch.p, energy ? (T *)g->meps.p : nullptr,
+                                         energy ? (T *)g->mmu.p : nullptr, s, (g->flags & FIT_FLAG_COEF_FLOAT) != 0));
+    else
     FIT_CHECK(build_coeffs<T>(g->nx, g->ny, g->nz, g->pitch, g->d, g->eps, g->mu, g->sig, dt, scheme, g->mu_array,
                               ca, cb, (T *)g->ch.p, energy ? (T *)g->meps.p : nullptr,
                               energy ? (T *)g->mmu.p : nullptr, s, (g->flags & FIT_FLAG_COEF_FLOAT) != 0));
@@ -618,11 +628,16 @@ struct ExpoParams {
     double u, c;   // u = dt/dt_CFL, c = q u
 };
 
+// 2/beta, beta the bound on ||A||_2 the propagators interpolate on: 2/dt_CFL on a uniform grid
+// (the Yee bound eq. (cfl) comes from), ||A||_1 on a graded grid (where eq. (cfl) is only an
+// estimate)
+double expo_unit(const fit_grid *g) { return g->graded ? 2.0 / g->rowsum : cfl_of(g); }
+
 int expo_params(const fit_grid *g, double dt, const fit_run_opts *o, ExpoParams *P) {
     const int kind = o ? o->homogeneous : FIT_HOMOG_LEAPFROG;
     if (kind != FIT_HOMOG_LEJA && kind != FIT_HOMOG_TAYLOR) return FIT_ERR_ARG;
     P->kind = kind;
-    P->u = dt / cfl_of(g);
+    P->u = dt / expo_unit(g);
     const double tol = (o->expo_tol > 0.0) ? o->expo_tol : (g->prec == 64 ? 1e-12 : 1e-6);
     if (!std::isfinite(tol)) return FIT_ERR_ARG;
     if (o->expo_substep > 0 || o->expo_degree > 0) {
@@ -742,10 +757,10 @@ int expo_members(fit_grid *g, double dt, const ExpoParams &X, const std::vector<
     a.nx = g->nx; a.ny = g->ny; a.nz = g->nz; a.pitch = g->pitch; a.ncp = ncp;
     a.cb = (const T *)g->coef.p;
     a.ch = (const T *)g->ch.p;
-    a.kappa = cfl_of(g) / dt;
+    a.kappa = expo_unit(g) / dt;
     a.mem = (const ExpoMember<T> *)(dt_base + o_mem);
     a.reg = (const double *)(dt_base + o_reg);
-    a.sync = dt / (2.0 * cfl_of(g));
+    a.sync = dt / (2.0 * expo_unit(g));
     a.m1 = m1;
     if ((rc = ensure(g->err, sizeof(int)))) return rc;
     a.err = (int *)g->err.p;
@@ -1601,6 +1616,48 @@ int fit_grid_create(int nx, int ny, int nz, double dx, double dy, double dz, con
     return FIT_OK;
 }
 
+int fit_grid_create_graded(int nx, int ny, int nz, const double *dx, const double *dy, const double *dz,
+                           const float *eps_r, const float *mu_r, const float *sigma, int precision, unsigned flags,
+                           fit_grid **out) {
+    if (!out) return FIT_ERR_ARG;
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1 || !dx || !dy || !dz) return FIT_ERR_ARG;
+    const double *ds[3] = {dx, dy, dz};
+    const int n[3] = {nx, ny, nz};
+    std::vector<double> spc;
+    double mean[3] = {0, 0, 0};
+    for (int a = 0; a < 3; ++a)
+        for (int i = 0; i < n[a]; ++i) {
+            const double v = ds[a][i];
+            if (!(v > 0.0) || !std::isfinite(v)) return FIT_ERR_ARG;
+            spc.push_back(v);
+            mean[a] += v / n[a];
+        }
+    fit_grid *g = nullptr;
+    int rc = fit_grid_create(nx, ny, nz, mean[0], mean[1], mean[2], eps_r, mu_r, sigma, precision, flags, &g);
+    if (rc) return rc;
+    if (ensure(g->spc, spc.size() * sizeof(double)) ||
+        cudaMemcpy(g->spc.p, spc.data(), spc.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+        fit_grid_destroy(g);
+        return FIT_ERR_OOM;
+    }
+    g->graded = true;
+    g->mu_array = true;   // ch varies per face
+    if (graded_cfl_and_bound(nx, ny, nz, (const double *)g->spc.p, g->eps, g->mu, g->scratch.p, &g->cfl_graded,
+                             &g->rowsum, 0) != cudaSuccess) {
+        fit_grid_destroy(g);
+        return FIT_ERR_CUDA;
+    }
+    *out = g;
+    return FIT_OK;
+}
+
+int fit_spectral_bound(const fit_grid *g, double *beta) {
+    if (!g || !beta) return FIT_ERR_ARG;
+    *beta = 2.0 / expo_unit(g);
+    return FIT_OK;
+}
+
 void fit_grid_destroy(fit_grid *g) {
     if (!g) return;
     cudaDeviceSynchronize();
@@ -1610,7 +1667,7 @@ void fit_grid_destroy(fit_grid *g) {
     Buf *bufs[] = {&g->coef, &g->ch, &g->meps, &g->mmu, &g->state, &g->pm, &g->amp, &g->srcdev,
                    &g->memdev, &g->acc, &g->kahan, &g->stage, &g->energy, &g->scratch, &g->probe_ws, &g->err,
                    &g->ckpt, &g->ring, &g->lam, &g->gacc, &g->aprobe, &g->aamp, &g->adjmem, &g->scalar,
-                   &g->grad_ws, &g->xblocks, &g->xtab, &g->xbasis, &g->xpm};
+                   &g->grad_ws, &g->xblocks, &g->xtab, &g->xbasis, &g->xpm, &g->spc};
     for (Buf *b : bufs) release(*b);
     for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
     delete g;
@@ -1721,9 +1778,10 @@ int fit_adjoint_grad(fit_grid *g, double dt, long nsteps, const fit_source *src,
     if ((rc = check_sources_probes(g, src, nsrc, prb, nprb))) return rc;
     if (opts && (opts->sigma_scheme < 0 || opts->sigma_scheme > 1)) return FIT_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
+    if (g->graded) return FIT_ERR_UNSUPPORTED;
     if (g->prec == 64)
         return adjoint_impl<double>(g, dt, nsteps, src, nsrc, prb, nprb, ckpt_every, J_out, grad_eps_r, opts, s);
-    if (g->prec == 48) return FIT_ERR_UNSUPPORTED;
+    if (g->prec == 48 || g->graded) return FIT_ERR_UNSUPPORTED;
     return adjoint_impl<float>(g, dt, nsteps, src, nsrc, prb, nprb, ckpt_every, J_out, grad_eps_r, opts, s);
 }
 

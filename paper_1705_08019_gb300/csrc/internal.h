@@ -181,6 +181,15 @@ cudaError_t join_pairs(int nx, int ny, int nz, int pitch, const float *hi, const
                        cudaStream_t s);
 cudaError_t accumulate_pairs(long long n, const float *hi, const float *lo, double *acc, cudaStream_t s);
 
+// graded.cu: tensor-product graded grids (spc_dev: nx + ny + nz sizes, x then y then z)
+template <typename T>
+cudaError_t build_coeffs_graded(int nx, int ny, int nz, int pitch, const double *spc_dev, const float *eps,
+                                const float *mu, const float *sig, double dt, int scheme, T *ca, T *cb, T *ch,
+                                T *meps, T *mmu, cudaStream_t s, bool round_float);
+// eq. (cfl) with per-cell sizes, and max |row sum| of A (= ||A||_1); scratch: 16 bytes
+cudaError_t graded_cfl_and_bound(int nx, int ny, int nz, const double *spc_dev, const float *eps, const float *mu,
+                                 void *scratch, double *cfl, double *rowsum_max, cudaStream_t s);
+
 // expo_plan.cu: host side of the Leja / Taylor propagators
 constexpr int kExpoMaxDegree = 120;
 // (q, m) for dt/dt_CFL = u; FIT_OK or FIT_ERR_ARG.  Cached per argument set.

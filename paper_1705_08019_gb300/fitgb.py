@@ -35,7 +35,7 @@ HOMOG = {"leapfrog": HOMOG_LEAPFROG, "leja": HOMOG_LEJA, "taylor": HOMOG_TAYLOR}
 EXPORTED = ("fit_grid_create", "fit_grid_destroy", "fit_cfl_dt", "fit_grid_info", "fit_leapfrog_run",
             "paraexp_run", "paraexp_run_batched", "fit_adjoint_grad", "fit_sync", "fit_strerror",
             "fit_version", "fit_last_stats", "fit_leapfrog_run_static", "fit_expo_plan", "fit_expo_coeffs",
-            "fit_expo_propagate")
+            "fit_expo_propagate", "fit_grid_create_graded", "fit_spectral_bound")
 
 
 class FitError(RuntimeError):
@@ -95,6 +95,10 @@ def load():
         I, L, D, P, U = ctypes.c_int, ctypes.c_long, ctypes.c_double, ctypes.c_void_p, ctypes.c_uint
         lib.fit_grid_create.argtypes = [I, I, I, D, D, D, P, P, P, I, U, ctypes.POINTER(P)]
         lib.fit_grid_create.restype = I
+        lib.fit_grid_create_graded.argtypes = [I, I, I, P, P, P, P, P, P, I, U, ctypes.POINTER(P)]
+        lib.fit_grid_create_graded.restype = I
+        lib.fit_spectral_bound.argtypes = [P, ctypes.POINTER(D)]
+        lib.fit_spectral_bound.restype = I
         lib.fit_grid_destroy.argtypes = [P]
         lib.fit_grid_destroy.restype = None
         lib.fit_cfl_dt.argtypes = [P, ctypes.POINTER(D)]
@@ -223,6 +227,37 @@ def fit_grid_create(dims, spacing, eps_r, mu_r=None, sigma=None, precision=32, f
                                 int(precision), int(flags), ctypes.byref(out))
     _check(rc, "fit_grid_create")
     return out.value
+
+
+def fit_grid_create_graded(dims, sizes, eps_r, mu_r=None, sigma=None, precision=32, flags=0):
+    """Graded grid: sizes = (dx[nx], dy[ny], dz[nz]) per-cell sizes in metres."""
+    nx, ny, nz = (int(v) for v in dims)
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in sizes]
+    if [a.size for a in arrs] != [nx, ny, nz]:
+        raise ValueError("one size per cell along each axis")
+    keep = list(arrs)
+
+    def f32(a):
+        if a is None:
+            return None
+        if isinstance(a, np.ndarray):
+            a = np.ascontiguousarray(a, dtype=np.float32)
+            if a.size != nx * ny * nz:
+                raise ValueError("material array has the wrong size")
+        keep.append(a)
+        return _addr(a)
+
+    out = ctypes.c_void_p()
+    rc = load().fit_grid_create_graded(nx, ny, nz, *(_addr(a) for a in arrs), f32(eps_r), f32(mu_r), f32(sigma),
+                                       int(precision), int(flags), ctypes.byref(out))
+    _check(rc, "fit_grid_create_graded")
+    return out.value
+
+
+def fit_spectral_bound(g):
+    v = ctypes.c_double()
+    _check(load().fit_spectral_bound(g, ctypes.byref(v)), "fit_spectral_bound")
+    return v.value
 
 
 def fit_grid_destroy(g):
@@ -354,11 +389,17 @@ class Grid:
 
     def __init__(self, dims, spacing, eps_r, mu_r=None, sigma=None, precision=32, flags=0):
         self.dims = tuple(int(v) for v in dims)
-        self.spacing = tuple(float(v) for v in spacing)
         self.precision = int(precision)
         # precision 48: compensated FP32 fields (hi + lo float pairs), FP64 I/O
         self.dtype = np.float64 if precision in (64, 48) else np.float32
-        self.handle = fit_grid_create(dims, spacing, eps_r, mu_r, sigma, precision, flags)
+        if all(np.ndim(v) == 0 for v in spacing):
+            self.spacing = tuple(float(v) for v in spacing)
+            self.handle = fit_grid_create(dims, spacing, eps_r, mu_r, sigma, precision, flags)
+        else:   # graded: per-cell sizes along each axis (a scalar stands for a constant axis)
+            sizes = [np.full(n, float(v)) if np.ndim(v) == 0 else np.asarray(v, np.float64)
+                     for n, v in zip(self.dims, spacing)]
+            self.spacing = tuple(sizes)
+            self.handle = fit_grid_create_graded(dims, sizes, eps_r, mu_r, sigma, precision, flags)
 
     @classmethod
     def from_workload(cls, w, precision=None):
@@ -371,6 +412,9 @@ class Grid:
 
     def cfl_dt(self):
         return fit_cfl_dt(self.handle)
+
+    def spectral_bound(self):
+        return fit_spectral_bound(self.handle)
 
     def leapfrog(self, dt, nsteps, sources=(), probes=(), step0=0, e=None, h=None, energy=False, opts=None):
         """Host-side convenience: returns (probes[n, p], energy | None, e, h) as numpy."""

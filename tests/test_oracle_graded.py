@@ -1,0 +1,161 @@
+"""Pins of the oracle on graded (tensor-product) grids: cell (i, j, k) of size
+dx[i] x dy[j] x dz[k] (Sec. II material matrices with local sizes, eq. (cfl)
+with each cell's own sizes, and the row-sum bound of A used by the
+exponential propagators).
+
+Pins from outside the oracle: the uniform grid as the limit of constant
+sizes, the closed-form energy of uniform fields (the dual cells tile the
+cells they cover), the dense matrix A built from the incidence definitions
+(tests/dense_fit.py) and its eigenvalues, scipy's expm."""
+import numpy as np
+import pytest
+import scipy.linalg as sl
+
+import oracle
+from oracle import expo
+from dense_fit import DenseFIT
+
+C0, MU0, EPS0 = oracle.constants()
+
+
+def rand_graded(dims, seed, ratio=4.0):
+    rng = np.random.default_rng(seed)
+    return [rng.uniform(1e-3 / ratio, 1e-3, n) for n in dims]
+
+
+def rand_materials(dims, seed, lossy=False, mu=True):
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = dims
+    eps = rng.uniform(1.0, 5.0, (nz, ny, nx)).astype(np.float32)
+    sig = rng.uniform(0.0, 2.0, (nz, ny, nx)).astype(np.float32) if lossy else None
+    mur = rng.uniform(1.0, 3.0, (nz, ny, nx)).astype(np.float32) if mu else None
+    return eps, mur, sig
+
+
+def dense_A(og):
+    d = DenseFIT((og.nx, og.ny, og.nz))
+    ie, ih = np.flatnonzero(d.edge_dof), np.flatnonzero(d.face_dof)
+    me, mm = og.meps.ravel()[ie], og.mmu.ravel()[ih]
+    top = -np.diag(mm ** -0.5) @ d.C[np.ix_(ih, ie)] @ np.diag(me ** -0.5)
+    A = np.block([[np.zeros((len(ih), len(ih))), top], [-top.T, np.zeros((len(ie), len(ie)))]])
+    return A, ie, ih, d
+
+
+def test_constant_sizes_reduce_to_the_uniform_grid():
+    dims = (5, 4, 6)
+    sp = (1e-3, 1.4e-3, 0.7e-3)
+    eps, mur, sig = rand_materials(dims, 3, lossy=True)
+    gu = oracle.OracleGrid(dims, sp, eps, mur, sig)
+    sizes = [np.full(n, v) for n, v in zip(dims, sp)]
+    gg = oracle.OracleGrid(dims, sizes, eps, mur, sig, dt=gu.dt)
+    assert gg.graded is not None
+    assert abs(oracle.cfl_dt(dims, sizes, eps, mur) / oracle.cfl_dt(dims, sp, eps, mur) - 1) <= 1e-15
+    for name in ("ca", "cb", "ch", "meps", "msig", "mmu"):
+        a, b = getattr(gg, name), getattr(gu, name)
+        assert np.max(np.abs(a - b)) <= 4e-16 * np.max(np.abs(b)), name
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_graded_material_matrices_give_exact_uniform_field_energy(axis):
+    """A uniform field E along `axis` (e = E d_a on every free edge) has the
+    discrete energy (1/2) e' M_eps e = (1/2) eps0 E^2 sum over cells of
+    eps_r V_cell (covered fraction): each free edge's dual cell holds a quarter
+    of each of its four cells.  A uniform B normal to `axis` (b = B A_face on
+    every interior face) has (1/2) b' M_mu^{-1} b = (1/2) B^2/mu0 sum over cells
+    of V_cell/mu_r (covered fraction), half of each of the face's two cells.
+    This fixes the dual areas, dual lengths and both averages on a graded
+    grid."""
+    dims = (5, 4, 6)
+    sizes = rand_graded(dims, 11, ratio=5.0)
+    eps, mur, _ = rand_materials(dims, 12)
+    g = oracle.OracleGrid(dims, sizes, eps, mur, None)
+    nx, ny, nz = dims
+    V = sizes[2][:, None, None] * sizes[1][None, :, None] * sizes[0][None, None, :]
+    b, c = (axis + 1) % 3, (axis + 2) % 3
+    E0, B0 = 3.0, 2e-6
+    Me = g.meps[axis]
+    W_disc = 0.0
+    cover = np.zeros((nz, ny, nx))
+    for k, j, i in np.ndindex(nz + 1, ny + 1, nx + 1):
+        if Me[k, j, i] == 0:
+            continue
+        q = (i, j, k)
+        W_disc += 0.5 * Me[k, j, i] * (E0 * sizes[axis][q[axis]]) ** 2
+        for sb in (0, 1):
+            for sc in (0, 1):
+                r = list(q); r[b] -= sb; r[c] -= sc
+                cover[r[2], r[1], r[0]] += 0.25
+    W_cont = 0.5 * EPS0 * E0 ** 2 * np.sum(eps * V * cover)
+    assert abs(W_disc - W_cont) <= 1e-13 * W_cont
+    Mm = g.mmu[axis]
+    W_disc = 0.0
+    cover = np.zeros((nz, ny, nx))
+    for k, j, i in np.ndindex(nz + 1, ny + 1, nx + 1):
+        if Mm[k, j, i] == 0:
+            continue
+        q = (i, j, k)
+        A = sizes[b][q[b]] * sizes[c][q[c]]
+        W_disc += 0.5 * (B0 * A) ** 2 / Mm[k, j, i]
+        cover[k, j, i] += 0.5
+        r = list(q); r[axis] -= 1
+        cover[r[2], r[1], r[0]] += 0.5
+    W_cont = 0.5 * B0 ** 2 / MU0 * np.sum(V * cover / mur)
+    assert abs(W_disc - W_cont) <= 1e-13 * W_cont
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+def test_row_sum_bound_and_cfl_estimate_on_graded_grids(seed):
+    """The oracle's row sums are those of the dense A; their maximum bounds
+    every eigenvalue; and eq. (cfl) with local sizes leaves the leapfrog
+    stable (dt_CFL <= 2/||A||_2) on these grids."""
+    dims = (4, 5, 3)
+    sizes = rand_graded(dims, 20 + seed, ratio=6.0)
+    if seed == 4:   # one thin slab
+        sizes = [np.full(n, 1e-3) for n in dims]
+        sizes[0][2] = 1e-4
+    eps, mur, _ = rand_materials(dims, 30 + seed)
+    g = oracle.OracleGrid(dims, sizes, eps, mur, None)
+    A, ie, ih, d = dense_A(g)
+    rs, oe, oh = g.A_rowsum()
+    dense_rows = np.abs(A).sum(1)
+    assert np.allclose(oh.ravel()[ih], dense_rows[: len(ih)], rtol=1e-14, atol=0)
+    assert np.allclose(oe.ravel()[ie], dense_rows[len(ih):], rtol=1e-14, atol=0)
+    assert abs(rs / dense_rows.max() - 1) <= 1e-14
+    lam = np.abs(np.linalg.eigvals(A)).max()
+    assert lam <= rs * (1 + 1e-12)
+    dtc = oracle.cfl_dt(dims, sizes, eps, mur)
+    assert lam * dtc / 2 < 1.0
+
+
+def test_graded_leapfrog_conserves_energy():
+    dims = (8, 7, 9)
+    sizes = rand_graded(dims, 41, ratio=8.0)
+    eps, mur, _ = rand_materials(dims, 42)
+    g = oracle.OracleGrid(dims, sizes, eps, mur, None, cfl_fraction=0.99)
+    t = 20 * g.dt
+    src = [dict(axis=2, i=4, j=3, k=4, waveform=1, amp=1.0, width=t, delay=t)]
+    _, en, _, _ = g.leapfrog(600, src, [], energy=True)
+    tail = en[150:]
+    assert tail.min() > 0 and np.ptp(tail) <= 1e-11 * tail.mean()
+
+
+def test_graded_propagate_equals_dense_exponential():
+    dims = (4, 4, 3)
+    sizes = rand_graded(dims, 51, ratio=5.0)
+    eps, mur, _ = rand_materials(dims, 52)
+    g = oracle.OracleGrid(dims, sizes, eps, mur, None)
+    beta = expo.spectral_bound(g)
+    assert beta == g.A_rowsum()[0]
+    A, ie, ih, d = dense_A(g)
+    rng = np.random.default_rng(3)
+    e0 = np.where(d.edge_dof, rng.standard_normal(d.N), 0.0).reshape(g.field_shape)
+    h0 = np.where(d.face_dof, rng.standard_normal(d.N), 0.0).reshape(g.field_shape)
+    n = 40
+    _, ef, hf = expo.propagate(g, n, e0, h0, (), "leja", tol=1e-12)
+    se, sh = np.sqrt(g.meps).ravel(), np.sqrt(g.mmu).ravel()
+    u0 = np.concatenate([(sh * h0.ravel())[ih], (se * e0.ravel())[ie]])
+    u = sl.expm(n * g.dt * A) @ u0
+    e = np.zeros(d.N); e[ie] = u[len(ih):] / se[ie]
+    h = np.zeros(d.N); h[ih] = u[: len(ih)] / sh[ih]
+    assert np.linalg.norm(ef.ravel() - e) <= 1e-10 * np.linalg.norm(e)
+    assert np.linalg.norm(hf.ravel() - h) <= 1e-10 * np.linalg.norm(h)
