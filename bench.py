@@ -55,6 +55,9 @@ def parse():
                          "lossless workload (default boxes256lossless): times, operator rate, roofline, "
                          "error against FP64 runs")
     ap.add_argument("--expo-tol", type=float, default=1e-6)
+    ap.add_argument("--rk-report", action="store_true",
+                    help="the non-uniform mesh cost study of Sec. IV-A: operator applications of Leja and "
+                         "leapfrog on the 2-D wave grid with its central element shrunk by k")
     ap.add_argument("--report", action="store_true",
                     help="accuracy run: FP32 ParaExp of the workload against an FP64 GPU reference "
                          "(float-rounded coefficients) over the first half of its windows")
@@ -615,8 +618,44 @@ def expo_report(args):
     print(json.dumps(out), flush=True)
 
 
+def rk_report(args):
+    """R(k) = C_Leja(k) / C_LF(k) on the 2-D wave grid of Sec. IV-A with the
+    central element shrunk to (d/k) x (d/k), over T = 2e-7 s.  Leapfrog takes
+    the step of eq. (cfl); Leja interpolates on the library's bound
+    beta = ||A||_1 (fit_spectral_bound) with the planned substep and degree
+    at tolerance eps_A (one substep count per output step of the leapfrog
+    grid).  Counts are applications of A (a leapfrog step applies C and C~
+    once: one application; the paper's C_LF = 2 n_t counts C and C~
+    separately, reported as well)."""
+    from paper_1705_08019_gb300 import build as B
+    from paper_1705_08019_gb300 import fitgb
+    from paper_1705_08019_gb300 import workloads as W
+    B.build()
+    fitgb.load()
+    T = 2e-7
+    rows = []
+    for tol in (1e-2, 1e-8):
+        for k in (1, 2, 3, 4, 6, 8, 10, 12, 14, 16, 18, 20):
+            w = W.wave2d_graded(k)
+            g = fitgb.fit_grid_create_graded(w.dims, w.spacing, w.eps_r, None, None, 64)
+            dtc = fitgb.fit_cfl_dt(g)
+            beta = fitgb.fit_spectral_bound(g)
+            fitgb.fit_grid_destroy(g)
+            n_lf = int(np.ceil(T / dtc))
+            u = dtc * beta / 2
+            q, m = fitgb.fit_expo_plan("leja", u, tol, 64)
+            n_leja = m * int(np.ceil(n_lf / q))
+            rows.append({"tol": tol, "k": k, "dt_cfl": dtc, "beta_times_dt_cfl_over_2": u, "leapfrog_steps": n_lf,
+                         "leja_q": q, "leja_m": m, "leja_applications": n_leja, "R": n_leja / n_lf,
+                         "R_paper_count": n_leja / (2 * n_lf)})
+    print(json.dumps({"study": "R(k), 2-D wave grid, central element d/k", "T": T, "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
+    if args.rk_report:
+        rk_report(args)
+        return
     if args.expo_report:
         expo_report(args)
         return

@@ -201,6 +201,23 @@ def wave2d(n_xy: int = 40, nsteps: int = 180) -> Workload:
         nsteps=nsteps, cfl_fraction=1.0, K=6, precision=64)
 
 
+def wave2d_graded(k: float, n_xy: int = 40) -> Workload:
+    """The 2-D wave grid of Sec. IV-A with its central element shrunk to
+    (d/k) x (d/k): on a tensor-product grid that makes the central column
+    and row of cells d/k wide, so the ratio of the largest to the smallest
+    element size is k (the non-uniform study of Sec. IV-A, R(k))."""
+    w = wave2d(n_xy=n_xy)
+    d = 20.0 / n_xy
+    c = n_xy // 2
+    dx = np.full(n_xy, d)
+    dy = np.full(n_xy, d)
+    dx[c] = d / k
+    dy[c] = d / k
+    w.spacing = (dx, dy, np.array([1.0]))
+    w.name = f"wave2d_k{k:g}"
+    return w
+
+
 def small_random(dims=(12, 10, 8), spacing=(1e-3, 1.2e-3, 0.9e-3), seed: int = SEED, lossy=True,
                  mu=False, nsteps: int = 200, K: int = 4, precision: int = 64) -> Workload:
     """Small non-cubic grid with random eps (and sigma, mu) for parity tests."""
@@ -217,6 +234,16 @@ def small_random(dims=(12, 10, 8), spacing=(1e-3, 1.2e-3, 0.9e-3), seed: int = S
     return Workload(name=f"small{nx}x{ny}x{nz}", dims=dims, spacing=spacing, eps_r=eps, mu_r=mu_r,
                     sigma=sig, sources=srcs, probes=prbs, nsteps=nsteps, cfl_fraction=0.95, K=K,
                     precision=precision)
+
+
+def graded_random(dims=(37, 19, 26), seed: int = SEED + 3, lossy=True, mu=True, ratio: float = 6.0) -> Workload:
+    """small_random with per-cell sizes drawn in [1 mm / ratio, 1 mm] along
+    every axis (a graded grid)."""
+    w = small_random(dims=dims, seed=seed, lossy=lossy, mu=mu, precision=64)
+    rng = _rng(seed + 1)
+    w.spacing = tuple(rng.uniform(1e-3 / ratio, 1e-3, n) for n in dims)
+    w.name = "graded" + w.name[5:]
+    return w
 
 
 def random_state(dims, seed: int = SEED + 7, dtype=np.float64):
