@@ -55,6 +55,9 @@ def parse():
                          "lossless workload (default boxes256lossless): times, operator rate, roofline, "
                          "error against FP64 runs")
     ap.add_argument("--expo-tol", type=float, default=1e-6)
+    ap.add_argument("--adjoint-report", action="store_true",
+                    help="time the adjoint gradient of the 128^3 workload (10^4 steps, checkpoints every 100) "
+                         "against one forward leapfrog run")
     ap.add_argument("--rk-report", action="store_true",
                     help="the non-uniform mesh cost study of Sec. IV-A: operator applications of Leja and "
                          "leapfrog on the 2-D wave grid with its central element shrunk by k")
@@ -651,8 +654,47 @@ def rk_report(args):
     print(json.dumps({"study": "R(k), 2-D wave grid, central element d/k", "T": T, "rows": rows}), flush=True)
 
 
+def adjoint_report(args):
+    """Seconds of fit_adjoint_grad (forward with checkpoints, recompute, reverse
+    sweep, gradient) on the 128^3 workload against one forward leapfrog run of
+    the same steps, FP32, device-resident inputs."""
+    import torch
+    from paper_1705_08019_gb300 import build as B
+    from paper_1705_08019_gb300 import fitgb
+    from paper_1705_08019_gb300 import workloads as W
+    B.build()
+    fitgb.load()
+    w = W.adjoint128()
+    dev = torch.device("cuda", 0)
+    s = torch.cuda.current_stream(dev)
+    eps = torch.from_numpy(w.eps_r).to(dev)
+    sig = torch.from_numpy(w.sigma).to(dev)
+    g = fitgb.fit_grid_create(w.dims, w.spacing, eps, None, sig, 32)
+    dt = w.cfl_fraction * fitgb.fit_cfl_dt(g)
+    J = torch.zeros(1, dtype=torch.float64, device=dev)
+    grad = torch.zeros(tuple(reversed(w.dims)), dtype=torch.float64, device=dev)
+    pr = torch.zeros((w.nsteps, len(w.probes)), dtype=torch.float64, device=dev)
+    out = {"workload": w.name, "cells": w.ncells, "nsteps": w.nsteps, "checkpoint_every": 100}
+    for name, fn in (("forward_s", lambda: fitgb.fit_leapfrog_run(g, dt, w.nsteps, 0, w.sources, w.probes, pr,
+                                                                   stream=s)),
+                     ("adjoint_s", lambda: fitgb.fit_adjoint_grad(g, dt, w.nsteps, w.sources, w.probes, 100, J, grad,
+                                                                  stream=s))):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        out[name] = time.perf_counter() - t0
+    out["adjoint_over_forward"] = out["adjoint_s"] / out["forward_s"]
+    fitgb.fit_grid_destroy(g)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.adjoint_report:
+        adjoint_report(args)
+        return
     if args.rk_report:
         rk_report(args)
         return

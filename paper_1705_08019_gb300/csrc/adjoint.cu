@@ -76,6 +76,27 @@ __global__ void grad_accum_kernel(long long ncp, const T *mu, const T *e1, const
     }
 }
 
+// the same into an FP32 block sum (FP32 fields): the FP64 total then takes one
+// read-modify-write per block of steps instead of one per step
+__global__ void grad_accum_block_kernel(long long ncp, const float *mu, const float *e1, const float *e0, float k0,
+                                        float k1, float k2, float *gb) {
+    const long long n3 = 3 * ncp;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n3;
+         c += (long long)gridDim.x * blockDim.x) {
+        const float prod = mu[c] * (e1[c] - e0[c]);
+        const float k = c < ncp ? k0 : (c < 2 * ncp ? k1 : k2);
+        gb[c] += k * prod;
+    }
+}
+
+__global__ void grad_flush_kernel(long long n3, float *gb, double *g) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n3;
+         c += (long long)gridDim.x * blockDim.x) {
+        g[c] += (double)gb[c];
+        gb[c] = 0.f;
+    }
+}
+
 // dJ/d eps_r(cell) = 1/4 sum over the 12 edges around the cell of g_edge
 __global__ void scatter_kernel(int nx, int ny, int nz, int pitch, long long ncp, const double *g, double *grad) {
     const long long ncell = (long long)nx * ny * nz;
@@ -148,6 +169,18 @@ template <typename T>
 cudaError_t grad_accumulate(long long ncp, const T *mu, const T *e1, const T *e0, const double k[3], double *g,
                             cudaStream_t s) {
     grad_accum_kernel<T><<<grid_for(3 * ncp), kThreads, 0, s>>>(ncp, mu, e1, e0, k[0], k[1], k[2], g);
+    return cudaGetLastError();
+}
+
+cudaError_t grad_accumulate_block(long long ncp, const float *mu, const float *e1, const float *e0, const double k[3],
+                                  float *gb, cudaStream_t s) {
+    grad_accum_block_kernel<<<grid_for(3 * ncp), kThreads, 0, s>>>(ncp, mu, e1, e0, (float)k[0], (float)k[1],
+                                                                   (float)k[2], gb);
+    return cudaGetLastError();
+}
+
+cudaError_t grad_flush(long long ncp, float *gb, double *g, cudaStream_t s) {
+    grad_flush_kernel<<<grid_for(3 * ncp), kThreads, 0, s>>>(3 * ncp, gb, g);
     return cudaGetLastError();
 }
 

@@ -57,7 +57,7 @@ struct fit_grid {
     Buf coef, ch, meps, mmu;   // coef: cb (3 components) then ca (3, lossy only)
     // workspaces
     Buf state, pm, amp, srcdev, memdev, acc, kahan, stage, energy, scratch, probe_ws, err;
-    Buf ckpt, ring, lam, gacc, aprobe, aamp, adjmem, scalar, grad_ws;   // adjoint workspaces
+    Buf ckpt, ring, lam, gacc, gblk, aprobe, aamp, adjmem, scalar, grad_ws;   // adjoint workspaces
     Buf xblocks, xtab, xbasis, xpm;   // exponential propagators: state blocks, tables, probe basis, probe rows
     int deferred = 0;
     Tile tile = {32, 8, 32, 2};
@@ -1058,6 +1058,12 @@ int adjoint_impl(fit_grid *g, double dt, long long N, const fit_source *src, int
     if ((rc = ensure(g->ring, (size_t)(C + 1) * n6 * sizeof(T)))) return rc;
     if ((rc = ensure(g->lam, 2 * n6 * sizeof(T)))) return rc;
     if ((rc = ensure(g->gacc, 3 * (size_t)ncp * sizeof(double)))) return rc;
+    // FP32 fields: the gradient of each block of kGradBlock adjoint steps is summed in FP32 and
+    // then added into the FP64 total (block boundaries fixed in the adjoint step index, so the
+    // result does not depend on the checkpoint interval)
+    constexpr int kGradBlock = 64;
+    const bool fp32_blocks = sizeof(T) == 4;
+    if (fp32_blocks && (rc = ensure(g->gblk, 3 * (size_t)ncp * sizeof(float)))) return rc;
     if ((rc = ensure(g->aprobe, (size_t)N * nprb * sizeof(double)))) return rc;
     if ((rc = ensure(g->aamp, (size_t)N * nprb * sizeof(double)))) return rc;
     if ((rc = ensure(g->adjmem, (size_t)(C + 2) * sizeof(Member)))) return rc;
@@ -1075,6 +1081,7 @@ int adjoint_impl(fit_grid *g, double dt, long long N, const fit_source *src, int
     FIT_CHECK(cudaMemsetAsync(ring, 0, n6 * sizeof(T), s));
     FIT_CHECK(cudaMemsetAsync(lam, 0, 2 * n6 * sizeof(T), s));
     FIT_CHECK(cudaMemsetAsync(gacc, 0, 3 * (size_t)ncp * sizeof(double), s));
+    if (fp32_blocks) FIT_CHECK(cudaMemsetAsync(g->gblk.p, 0, 3 * (size_t)ncp * sizeof(float), s));
     FIT_CHECK(cudaMemsetAsync(g->err.p, 0, sizeof(int), s));
 
     // member table: [0] forward ping-pong in ring slots 0/1, [1+q] ring slot q -> q+1,
@@ -1190,9 +1197,19 @@ int adjoint_impl(fit_grid *g, double dt, long long N, const fit_source *src, int
             a.parity = (int)(t & 1);
             FIT_CHECK(step(lam_maps));
             const T *mu_in = lam + (size_t)(t & 1) * n6;
-            FIT_CHECK(grad_accumulate<T>(ncp, mu_in, ring + (size_t)(n + 1 - A) * n6, ring + (size_t)(n - A) * n6, K,
-                                         gacc, s));
-            g->stats.kernel_launches += 1;
+            if (fp32_blocks) {
+                FIT_CHECK(grad_accumulate_block(ncp, (const float *)mu_in, (const float *)(ring + (size_t)(n + 1 - A) * n6),
+                                                (const float *)(ring + (size_t)(n - A) * n6), K, (float *)g->gblk.p, s));
+                g->stats.kernel_launches += 1;
+                if ((t + 1) % kGradBlock == 0 || t == N - 1) {
+                    FIT_CHECK(grad_flush(ncp, (float *)g->gblk.p, gacc, s));
+                    g->stats.kernel_launches += 1;
+                }
+            } else {
+                FIT_CHECK(grad_accumulate<T>(ncp, mu_in, ring + (size_t)(n + 1 - A) * n6, ring + (size_t)(n - A) * n6,
+                                             K, gacc, s));
+                g->stats.kernel_launches += 1;
+            }
         }
     }
     // per-cell gradient and J
@@ -1667,7 +1684,7 @@ void fit_grid_destroy(fit_grid *g) {
     Buf *bufs[] = {&g->coef, &g->ch, &g->meps, &g->mmu, &g->state, &g->pm, &g->amp, &g->srcdev,
                    &g->memdev, &g->acc, &g->kahan, &g->stage, &g->energy, &g->scratch, &g->probe_ws, &g->err,
                    &g->ckpt, &g->ring, &g->lam, &g->gacc, &g->aprobe, &g->aamp, &g->adjmem, &g->scalar,
-                   &g->grad_ws, &g->xblocks, &g->xtab, &g->xbasis, &g->xpm, &g->spc};
+                   &g->grad_ws, &g->xblocks, &g->xtab, &g->xbasis, &g->xpm, &g->spc, &g->gblk};
     for (Buf *b : bufs) release(*b);
     for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
     delete g;

@@ -270,6 +270,10 @@ cudaError_t adjoint_sources(const fit_probe *prb, int nprb, const double d[3], c
 template <typename T>
 cudaError_t grad_accumulate(long long ncp, const T *mu, const T *e1, const T *e0, const double k[3], double *g,
                             cudaStream_t s);
+// FP32 fields: g_b += K mu (e1 - e0) in an FP32 block sum, added into the FP64 total by grad_flush
+cudaError_t grad_accumulate_block(long long ncp, const float *mu, const float *e1, const float *e0, const double k[3],
+                                  float *gb, cudaStream_t s);
+cudaError_t grad_flush(long long ncp, float *gb, double *g, cudaStream_t s);
 cudaError_t grad_scatter(int nx, int ny, int nz, int pitch, long long ncp, const double *g, double *grad,
                          cudaStream_t s);
 cudaError_t probe_functional(const fit_probe *prb, int nprb, const double d[3], const double *probe, long long N,
