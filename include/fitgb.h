@@ -123,6 +123,11 @@ typedef struct {
     double expo_tol;            /* Leja/Taylor: backward-error tolerance
                                    eps_A of ||Delta A|| <= eps_A ||A||
                                    [0 = 1e-12 for FP64 grids, 1e-6 for FP32]  */
+    int steps_per_launch;       /* FP32 leapfrog and ParaExp runs without
+                                   energy output: 2 advances every member two
+                                   steps per launch (temporal blocking: the
+                                   fields are read and written once per two
+                                   steps), 1 one step [0 = 1]                 */
 } fit_run_opts;
 
 /* Propagators of the homogeneous problems w_j (opts->homogeneous). */

@@ -330,6 +330,29 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
         return FIT_OK;
     };
 
+    // two steps per launch (FP32, TMA, no energy): the temporal-blocking kernel
+    bool two = false;
+    TmaMaps maps2;
+    CUtensorMap coefwin;
+    Tile tile2 = {32, 8, tile.kz, 2, 3};
+    if (opts && opts->steps_per_launch == 2 && sizeof(T) == 4 && !comp && !energy_dev && tile.kernel == 2) {
+        if (opts->tile_x > 0 && opts->tile_y > 0 && step2_tile_supported(opts->tile_x, opts->tile_y))
+            tile2.tx = opts->tile_x, tile2.ty = opts->tile_y;
+        two = encode_tma_maps(&maps2, 4, g->nx, g->ny, g->nz, g->pitch, g->state.p, 2 * mpp, g->coef.p,
+                              g->lossy ? 6 : 3, tile2.tx, tile2.ty + 2) &&
+              encode_window_map(&coefwin, 4, g->nx, g->ny, g->nz, g->pitch, g->coef.p, g->lossy ? 6 : 3,
+                                tile2.tx + 8, tile2.ty + 4, g->lossy ? 6 : 3);
+    }
+    StepArgs<T> a2 = a;
+    if (two) {
+        a2.tiles_x = (g->nx + tile2.tx - 1) / tile2.tx;
+        a2.tiles_y = (g->ny + tile2.ty - 1) / tile2.ty;
+        a2.kz = (opts && opts->tile_z > 0) ? opts->tile_z : 64;
+        const long long cols2 = (long long)a2.tiles_x * a2.tiles_y;
+        while (a2.kz > 8 && cols2 * ((g->nz + a2.kz - 1) / a2.kz) < 2 * 152) a2.kz /= 2;
+        a2.nchunk = (g->nz + a2.kz - 1) / a2.kz;
+    }
+
     // Groups run from the end of the table (shortest members) to its start, and
     // inside a group members finish shortest first, so the superposition adds
     // members in decreasing table order whatever members_per_pass is.
@@ -386,7 +409,67 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
 
         const long long nit_max = specs_in[order[first]].nit;
         int active = cnt;
-        for (long long it = 0; it < nit_max; ++it) {
+        // a member that took its last step in the launch just issued, whose final
+        // state is `fin`: superposition, copy-out, keep
+        auto finish_member = [&](int q, const T *fin) -> int {
+            if (acc_e) {
+                if (kahan) {
+                    float *ks = (float *)g->kahan.p;
+                    FIT_CHECK(accumulate_state_kahan<T>((long long)n6, fin, ks, ks + n6, s));
+                } else {
+                    FIT_CHECK(accumulate_state<T>(3 * ncp, fin, acc_e, s));
+                    if (acc_h) FIT_CHECK(accumulate_state<T>(3 * ncp, fin + 3 * ncp, acc_h, s));
+                }
+                g->stats.kernel_launches += 1;
+            }
+            if (order[first + q] == 0) {
+                int r2 = copy_out(fin);
+                if (r2) return r2;
+            }
+            if (keep_final && keep_final[order[first + q]])
+                FIT_CHECK(cudaMemcpyAsync(keep_final[order[first + q]], fin, n6 * sizeof(T), cudaMemcpyDeviceToDevice,
+                                          s));
+            return FIT_OK;
+        };
+        for (long long it = 0, L = 0; two && it < nit_max; it += 2, ++L) {
+            while (active > 0 && specs_in[order[first + active - 1]].nit <= it) --active;
+            a2.nmem = active;
+            a2.it = (int)it;
+            a2.parity = (int)(L & 1);
+            if (profile) {
+                while ((long long)g->ev.size() < 2 * (nev + 1)) {
+                    cudaEvent_t e;
+                    FIT_CHECK(cudaEventCreate(&e));
+                    g->ev.push_back(e);
+                }
+                FIT_CHECK(cudaEventRecord(g->ev[2 * nev], s));
+            }
+            FIT_CHECK(launch_step2_tma((const StepArgs<float> &)a2, maps2.state, coefwin, tile2.tx, tile2.ty, g->lossy,
+                                       g->mu_array, s));
+            if (profile) {
+                FIT_CHECK(cudaEventRecord(g->ev[2 * nev + 1], s));
+                ++nev;
+            }
+            g->stats.step_launches += 1;
+            g->stats.kernel_launches += 1;
+            // algorithmic bytes are counted per step as for the one-step kernel
+            int two_steps = 0;
+            for (int q = 0; q < active; ++q) {
+                const long long left = specs_in[order[first + q]].nit - it;
+                const int st = left >= 2 ? 2 : 1;
+                g->stats.cell_updates += (long long)st * ncell;
+                g->stats.alg_bytes += fld_bytes * st;
+                if (st == 2) two_steps = 1;
+            }
+            g->stats.alg_bytes += coef_bytes * (two_steps ? 2 : 1);
+            for (int q = active - 1; q >= 0; --q) {
+                const long long left = specs_in[order[first + q]].nit - it;
+                if (left > 2) continue;
+                int r2 = finish_member(q, (const T *)mem[q].st[(L + 1) & 1]);
+                if (r2) return r2;
+            }
+        }
+        for (long long it = 0; !two && it < nit_max; ++it) {
             while (active > 0 && specs_in[order[first + active - 1]].nit <= it) --active;
             a.nmem = active;
             a.it = (int)it;

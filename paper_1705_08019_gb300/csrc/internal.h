@@ -147,6 +147,12 @@ bool batched_tile_supported(int tx, int ty);
 bool encode_tma_maps(TmaMaps *out, int elem_bytes, int nx, int ny, int nz, int pitch, void *state,
                      int nblocks, const void *coef, int ncoef, int tx, int ty, int nstate = 6);
 
+// step2_tma.cu: two steps per launch (FP32, no energy); tm_state with the box (tx+8, ty+4, 1, 3, 1),
+// tm_coef the coefficient window (tx+8, ty+4, 1, 3 or 6)
+bool step2_tile_supported(int tx, int ty);
+cudaError_t launch_step2_tma(const StepArgs<float> &a, const CUtensorMap &tm_state, const CUtensorMap &tm_coef,
+                             int tx, int ty, bool lossy, bool muarr, cudaStream_t s);
+
 // step_comp.cu: compensated FP32 fields (hi + lo pairs, 12-component state blocks)
 cudaError_t launch_step_comp(const StepArgs<float> &a, const TmaMaps &maps, Tile tile, bool lossy, bool mu_array,
                              bool energy, cudaStream_t s);
