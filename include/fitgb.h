@@ -112,7 +112,8 @@ typedef struct {
     int debug_extra_tx;         /* test hook: bytes announced on top of the
                                    first plane's copies of every tile, so its
                                    wait can never complete and must time out
-                                   (FP32/FP64 TMA kernel) [0]                 */
+                                   (the TMA step kernels, one or two steps per
+                                   launch, and the fused Leja pair kernel) [0] */
     int homogeneous;            /* propagator of the homogeneous ParaExp
                                    problems: FIT_HOMOG_LEAPFROG, _LEJA or
                                    _TAYLOR (see paraexp_run) [LEAPFROG]       */

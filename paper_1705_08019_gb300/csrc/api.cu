@@ -847,6 +847,7 @@ int expo_members(fit_grid *g, double dt, const ExpoParams &X, const std::vector<
     a.m1 = m1;
     if ((rc = ensure(g->err, sizeof(int)))) return rc;
     a.err = (int *)g->err.p;
+    a.extra_tx = opts ? std::max(0, opts->debug_extra_tx) : 0;
     a.nprb = probes ? nprb : 0;
     for (int p = 0; p < a.nprb; ++p) a.prb[p] = {prb[p].axis, prb[p].i, prb[p].j, prb[p].k};
     // z chunks: enough blocks to fill the GPU with the fewest members of a launch

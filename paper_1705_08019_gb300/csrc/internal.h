@@ -235,6 +235,7 @@ struct ExpoArgs {
     double sync;            // dt/(2 dt_CFL): half magnetic step in units of X
     int m1;                 // m + 1 (probe basis rows per substep)
     int *err;               // device error word (bounded waits of the TMA pair kernel)
+    int extra_tx;           // test hook: bytes announced beyond a tile's first plane (TMA pair kernel)
     int nprb;
     EdgeRef prb[kMaxPrb];
 };

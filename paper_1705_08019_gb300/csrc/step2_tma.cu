@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(TX *TY) step2_tma_kernel(const __grid_constant
         const int kk = kstart + p;
         unsigned char *st = dsm + (p % S) * G::STAGE;
         uint64_t *b = &bar[p % S];
-        mbar_expect_tx(b, G::TX_BYTES);
+        mbar_expect_tx(b, G::TX_BYTES + (p == 0 ? (uint32_t)a.extra_tx : 0u));
         tma_load_5d(st, &tm_state, b, i0 - 4, j0 - 2, kk, 0, blk_in);
         tma_load_5d(st + G::H_OFF, &tm_state, b, i0 - 4, j0 - 2, kk, 3, blk_in);
         tma_load_4d(st + G::C_OFF, &tm_coef, b, i0 - 4, j0 - 2, kk, 0);

@@ -35,3 +35,38 @@ def test_bounded_wait_reports_timeout_and_recovers(precision):
     for a, b in zip(again, ref):
         if a is not None:
             assert np.array_equal(a, b)
+
+
+def test_two_step_kernel_timeout_and_recovery():
+    w = W.small_random(dims=(40, 20, 12), nsteps=6)
+    g = fitgb.Grid.from_workload(w, 32)
+    dt = 0.9 * g.cfl_dt()
+    ref = g.leapfrog(dt, w.nsteps, w.sources, w.probes, opts=fitgb.make_opts(steps_per_launch=2))
+    with pytest.raises(fitgb.FitError) as ei:
+        g.leapfrog(dt, w.nsteps, w.sources, w.probes,
+                   opts=fitgb.make_opts(steps_per_launch=2, debug_wait_limit=2000, debug_extra_tx=16))
+    assert ei.value.status == fitgb.FIT_ERR_TIMEOUT
+    again = g.leapfrog(dt, w.nsteps, w.sources, w.probes, opts=fitgb.make_opts(steps_per_launch=2))
+    g.close()
+    for a, b in zip(again, ref):
+        if a is not None:
+            assert np.array_equal(a, b)
+
+
+def test_fused_leja_pair_timeout_and_recovery():
+    w = W.small_random(dims=(40, 20, 12), lossy=False)
+    g = fitgb.Grid(w.dims, w.spacing, w.eps_r, None, None, 32)
+    dt = 0.9 * g.cfl_dt()
+    e0, h0 = W.random_state(w.dims, dtype=np.float32)
+    ref = g.expo_propagate(dt, 8, e0, h0, w.probes, "leja", q=4, m=8)
+    with pytest.raises(fitgb.FitError) as ei:
+        e, h = np.array(e0), np.array(h0)
+        pr = np.zeros((8, len(w.probes)))
+        fitgb.fit_expo_propagate(g.handle, dt, 8, w.probes, pr, e, h,
+                                 fitgb.make_opts(homogeneous="leja", expo_substep=4, expo_degree=8,
+                                                 debug_wait_limit=2000, debug_extra_tx=16))
+    assert ei.value.status == fitgb.FIT_ERR_TIMEOUT
+    again = g.expo_propagate(dt, 8, e0, h0, w.probes, "leja", q=4, m=8)
+    g.close()
+    for a, b in zip(again, ref):
+        assert np.array_equal(a, b)
