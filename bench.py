@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--compare-plain", action="store_true",
                     help="also time the K windows run one after another (members_per_pass=1)")
-    ap.add_argument("--ncu-case", choices=["leapfrog", "paraexp", "expo"], default=None,
+    ap.add_argument("--ncu-case", choices=["leapfrog", "paraexp", "expo", "batch"], default=None,
                     help="run a short untimed case for an ncu capture and exit (no JSON line)")
     ap.add_argument("--ncu-steps", type=int, default=8)
     ap.add_argument("--ncu-members", type=int, default=4)
@@ -375,6 +375,20 @@ def ncu_case(args):
     from paper_1705_08019_gb300 import build as B
     from paper_1705_08019_gb300 import fitgb
     B.build()
+    if args.ncu_case == "batch":
+        # 8 of the uneven cavities, K = 4, --ncu-steps steps: one persistent launch per step
+        from paper_1705_08019_gb300 import workloads as W
+        dev = torch.device("cuda", 0)
+        ws = W.cavity_batch(count=8, nsteps=args.ncu_steps, K=4)
+        gs = [fitgb.fit_grid_create(w.dims, w.spacing, torch.from_numpy(w.eps_r).to(dev), None, None, 32) for w in ws]
+        probs = [dict(grid=g, dt=w.cfl_fraction * fitgb.fit_cfl_dt(g), K=w.K, win=w.windows(), sources=w.sources,
+                      probes=w.probes) for g, w in zip(gs, ws)]
+        fitgb.paraexp_run_batched(probs, fitgb.make_opts(tile_x=32, tile_y=8, stages=4),
+                                  torch.cuda.current_stream(dev))
+        torch.cuda.synchronize()
+        for g in gs:
+            fitgb.fit_grid_destroy(g)
+        return
     w = load_workload(args.workload)
     dev = torch.device("cuda", 0)
     eps = torch.from_numpy(w.eps_r).to(dev)
