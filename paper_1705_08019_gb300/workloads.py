@@ -148,6 +148,22 @@ def boxes256_lossless(seed: int = SEED, nsteps: int = 2000, n_side: int = 256) -
     return boxes(n_side=n_side, seed=seed, nsteps=nsteps, K=16, name="boxes256lossless", lossy=False)
 
 
+def boxes_graded(k: float, n_side: int = 256, seed: int = SEED, nsteps: int = 2000) -> Workload:
+    """The lossless 256^3 boxes with the central slab of cells along each axis
+    shrunk to d/k (a strongly graded tensor-product grid; largest / smallest
+    cell size k)."""
+    w = boxes(n_side=n_side, seed=seed, nsteps=nsteps, K=16, name=f"boxes{n_side}_k{k:g}", lossy=False)
+    d = w.spacing[0]
+    c = n_side // 2
+    sizes = []
+    for _ in range(3):
+        a = np.full(n_side, d)
+        a[c] = d / k
+        sizes.append(a)
+    w.spacing = tuple(sizes)
+    return w
+
+
 def boxes512(seed: int = SEED, nsteps: int = 100000, n_side: int = 512) -> Workload:
     return boxes(n_side=n_side, seed=seed, nsteps=nsteps, K=32, side_scale=2.0, name="boxes512")
 
