@@ -12,9 +12,10 @@ import oracle
 # ~1e3 steps of O(10) flops each).
 TOL64 = 1e-11
 # FP32 paths are compared with the FP64 oracle run on the same float-rounded
-# coefficients.  The floor 1e-5 is the method's FP32 target.  Near a driven
-# source the curl of h nearly cancels the impressed current, so the rounding
-# of float-stored fields is amplified; no FP32-storage scheme can beat the
+# coefficients.  The floor 1e-5 is the method's FP32 target.  Rounding every
+# stored e and h value to float accumulates over the steps like a random
+# walk (about 6e-8 sqrt(steps) of the field), and more in relative terms for a
+# quantity whose own norm is small; no FP32-storage scheme can beat the
 # "store32" model (exact arithmetic, every stored e and h rounded to float).
 # The tolerance is therefore max(1e-5, FP32_FACTOR x the store32 model's own
 # error) per compared quantity: FP32 arithmetic in the curl sums and updates
