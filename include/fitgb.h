@@ -337,7 +337,9 @@ typedef struct {
 /* Many independent ParaExp problems (grids of any size) advanced together:
  * every member of every problem is one work item of a single persistent,
  * CUDA-graph-captured launch per block of iterations.  Results equal
- * paraexp_run on each problem alone. */
+ * paraexp_run on each problem alone.  With opts->homogeneous set to LEJA or
+ * TAYLOR, or opts->steps_per_launch = 2, the problems run one after another
+ * through paraexp_run instead. */
 int paraexp_run_batched(const fit_paraexp_problem *probs, int nprobs,
                         const fit_run_opts *opts, void *stream);
 

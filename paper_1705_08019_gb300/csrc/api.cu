@@ -1852,7 +1852,10 @@ int paraexp_run_batched(const fit_paraexp_problem *probs, int nprobs, const fit_
         for (int r = 0; r < p; ++r)
             if (probs[r].grid == q.grid) return FIT_ERR_ARG;
     }
-    const bool fused = !(opts && (opts->members_per_pass > 0 || opts->sum_mode != 0 || opts->kernel == 1));
+    // the persistent batched launch advances leapfrog members; exponential homogeneous problems
+    // (and the plain per-window comparison modes) run the problems one after another
+    const bool fused = !(opts && (opts->members_per_pass > 0 || opts->sum_mode != 0 || opts->kernel == 1 ||
+                                  opts->homogeneous != FIT_HOMOG_LEAPFROG || opts->steps_per_launch == 2));
     std::vector<const fit_paraexp_problem *> lossless, lossy;
     for (int p = 0; p < nprobs; ++p) {
         const fit_paraexp_problem &q = probs[p];

@@ -119,3 +119,15 @@ def test_fullsize_batch64_equals_plain_runs():
         assert torch.isfinite(a["probe_out"]).all() and a["probe_out"].abs().max() > 0
     for g in grids:
         g.close()
+
+
+def test_batched_with_leja_homogeneous_problems():
+    """opts.homogeneous reaches every problem of a batch: the results equal
+    paraexp_run with the same options, problem by problem."""
+    ws = [W.small_random(dims=d, lossy=False, K=3, nsteps=60, seed=200 + n)
+          for n, d in enumerate([(33, 17, 21), (20, 40, 9)])]
+    opts = fitgb.make_opts(homogeneous="leja", expo_tol=1e-8)
+    ref = run_problems(ws, batched=False, opts=opts)
+    assert_same(run_problems(ws, batched=True, opts=opts), ref)
+    lf = run_problems(ws, batched=False)
+    assert not np.array_equal(ref[0][0], lf[0][0])   # not the leapfrog result
