@@ -23,9 +23,16 @@ every workload is synthetic):
   steps, K=32, FP32.
 * ``wave2d``    the paper's 2-D cylindrical wave (Sec. IV-A): 20 m x 20 m x
   1 m, 40x40x1 cells, centred z line current, Gaussian pulse.
+* ``boxes256_lossless`` boxes256 without conductivity (2000 steps): the
+  exponential propagators need a lossless grid.
+* ``wave2d_graded(k)`` / ``boxes_graded(k)`` the 2-D wave grid and the
+  lossless 256^3 boxes with the central column/row (slab) of cells shrunk to
+  d/k: graded tensor-product grids for the non-uniform mesh study.
+* ``small_random`` / ``graded_random`` small non-cubic grids with random
+  eps_r, mu_r, sigma (and random per-cell sizes) for parity tests;
+  ``random_state`` seeded initial fields.
 
-Any workload can be shrunk with ``scale`` (cells per axis multiplied) and
-``nsteps`` overrides for tests.
+``nsteps`` and the grid size can be overridden for tests.
 """
 from __future__ import annotations
 
