@@ -1,0 +1,223 @@
+// adjoint_api.cu -- fit_adjoint_grad: the adjoint gradient's schedule on
+// the host (kernels in adjoint.cu and the fused step kernels).
+#include "grid.h"
+
+using namespace fitgb;
+
+namespace {
+
+// Adjoint gradient (see adjoint.cu for the reverse sweep and the gradient
+// formula).  Schedule: one forward pass of N steps from zero state records the
+// probe trace and a checkpoint of (e, h) every C steps; then, segment by
+// segment from the last, the checkpoint is re-advanced through a ring of
+// C+1 state slots (slot q holds step A+q), and the adjoint state steps back
+// through the segment, each adjoint step followed by the gradient update from
+// ring slots q and q+1.  Memory: N/C checkpoints + C+1 ring slots.
+template <typename T>
+int adjoint_impl(fit_grid *g, double dt, long long N, const fit_source *src, int nsrc, const fit_probe *prb,
+                 int nprb, int C, double *J_out, double *grad_out, const fit_run_opts *opts, cudaStream_t s) {
+    const int scheme = opts ? opts->sigma_scheme : 0;
+    int rc;
+    g->stats = fit_run_stats{0, 0, 0, 0.0, 0.0, 0, 0, 0.0, 0.0};
+    if (nprb < 1 || nprb > kMaxSrc || nsrc > kMaxSrc) return FIT_ERR_UNSUPPORTED;
+    if ((rc = ensure_coeffs<T>(g, dt, scheme, false, s))) return rc;
+    if (C <= 0) C = std::max(1, (int)std::ceil(std::sqrt((double)N)));
+    if (C > N) C = (int)N;
+    const long long nseg = (N + C - 1) / C;
+    const long long ncp = g->ncp;
+    const size_t n6 = 6 * (size_t)ncp;
+    if ((rc = ensure(g->ckpt, (size_t)nseg * n6 * sizeof(T)))) return rc;
+    if ((rc = ensure(g->ring, (size_t)(C + 1) * n6 * sizeof(T)))) return rc;
+    if ((rc = ensure(g->lam, 2 * n6 * sizeof(T)))) return rc;
+    if ((rc = ensure(g->gacc, 3 * (size_t)ncp * sizeof(double)))) return rc;
+    // FP32 fields: the gradient of each block of kGradBlock adjoint steps is summed in FP32 and
+    // then added into the FP64 total (block boundaries fixed in the adjoint step index, so the
+    // result does not depend on the checkpoint interval)
+    constexpr int kGradBlock = 64;
+    const bool fp32_blocks = sizeof(T) == 4;
+    if (fp32_blocks && (rc = ensure(g->gblk, 3 * (size_t)ncp * sizeof(float)))) return rc;
+    if ((rc = ensure(g->aprobe, (size_t)N * nprb * sizeof(double)))) return rc;
+    if ((rc = ensure(g->aamp, (size_t)N * nprb * sizeof(double)))) return rc;
+    if ((rc = ensure(g->adjmem, (size_t)(C + 2) * sizeof(Member)))) return rc;
+    if ((rc = ensure(g->err, sizeof(int)))) return rc;
+    if ((rc = ensure(g->scalar, 2 * sizeof(double)))) return rc;
+    if (nsrc > 0) {
+        if ((rc = ensure(g->amp, sizeof(double) * (size_t)N * nsrc))) return rc;
+        if ((rc = ensure(g->srcdev, sizeof(fit_source) * nsrc))) return rc;
+        FIT_CHECK(cudaMemcpyAsync(g->srcdev.p, src, sizeof(fit_source) * nsrc, cudaMemcpyHostToDevice, s));
+        FIT_CHECK(source_table((const fit_source *)g->srcdev.p, nsrc, 0, N, dt, (double *)g->amp.p, s));
+        g->stats.kernel_launches += 1;
+    }
+    T *ring = (T *)g->ring.p, *lam = (T *)g->lam.p, *ckpt = (T *)g->ckpt.p;
+    double *gacc = (double *)g->gacc.p, *aprobe = (double *)g->aprobe.p, *aamp = (double *)g->aamp.p;
+    FIT_CHECK(cudaMemsetAsync(ring, 0, n6 * sizeof(T), s));
+    FIT_CHECK(cudaMemsetAsync(lam, 0, 2 * n6 * sizeof(T), s));
+    FIT_CHECK(cudaMemsetAsync(gacc, 0, 3 * (size_t)ncp * sizeof(double), s));
+    if (fp32_blocks) FIT_CHECK(cudaMemsetAsync(g->gblk.p, 0, 3 * (size_t)ncp * sizeof(float), s));
+    FIT_CHECK(cudaMemsetAsync(g->err.p, 0, sizeof(int), s));
+
+    // member table: [0] forward ping-pong in ring slots 0/1, [1+q] ring slot q -> q+1,
+    // [C+1] the adjoint state's ping-pong
+    std::vector<Member> mt((size_t)C + 2);
+    memset(mt.data(), 0, sizeof(Member) * mt.size());
+    for (auto &m : mt) {
+        m.src_lo = -(1LL << 62);
+        m.src_hi = (1LL << 62);
+        m.end = (1LL << 62);
+    }
+    mt[0].st[0] = ring;
+    mt[0].st[1] = ring + n6;
+    mt[0].blk[0] = 0;
+    mt[0].blk[1] = 1;
+    mt[0].probe = aprobe;
+    for (int q = 0; q < C; ++q) {
+        Member &m = mt[1 + q];
+        m.st[0] = ring + (size_t)q * n6;
+        m.st[1] = ring + (size_t)(q + 1) * n6;
+        m.blk[0] = q;
+        m.blk[1] = q + 1;
+        m.start = q;   // + the segment start passed as the iteration
+    }
+    mt[C + 1].st[0] = lam;
+    mt[C + 1].st[1] = lam + n6;
+    mt[C + 1].blk[0] = 0;
+    mt[C + 1].blk[1] = 1;
+    Member *mdev = (Member *)g->adjmem.p;
+    FIT_CHECK(cudaMemcpyAsync(mdev, mt.data(), sizeof(Member) * mt.size(), cudaMemcpyHostToDevice, s));
+
+    Tile tile = pick_tile(g, opts);
+    TmaMaps ring_maps, lam_maps;
+    if (tile.kernel == 2 &&
+        !(encode_tma_maps(&ring_maps, (int)sizeof(T), g->nx, g->ny, g->nz, g->pitch, ring, C + 1, g->coef.p,
+                          g->lossy ? 6 : 3, tile.tx, tile.ty) &&
+          encode_tma_maps(&lam_maps, (int)sizeof(T), g->nx, g->ny, g->nz, g->pitch, lam, 2, g->coef.p,
+                          g->lossy ? 6 : 3, tile.tx, tile.ty))) {
+        tile.kernel = 1;
+        if (!tile_supported(tile.tx, tile.ty)) tile.tx = 32, tile.ty = 8;
+    }
+    StepArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    a.nx = g->nx; a.ny = g->ny; a.nz = g->nz; a.pitch = g->pitch; a.ncell = ncp;
+    a.tiles_x = (g->nx + tile.tx - 1) / tile.tx;
+    a.tiles_y = (g->ny + tile.ty - 1) / tile.ty;
+    a.kz = tile.kz;
+    a.nchunk = (g->nz + tile.kz - 1) / tile.kz;
+    a.cb = (const T *)g->coef.p;
+    a.ca = g->lossy ? (const T *)g->coef.p + 3 * ncp : nullptr;
+    a.ch = (const T *)g->ch.p;
+    a.nmem = 1;
+    a.err = (int *)g->err.p;
+    auto step = [&](const TmaMaps &maps) -> cudaError_t {
+        g->stats.step_launches += 1;
+        g->stats.kernel_launches += 1;
+        g->stats.cell_updates += g->ncell;
+        if (tile.kernel == 2) return launch_step_tma<T>(a, maps, tile, g->lossy, g->mu_array, false, s);
+        return launch_step<T>(a, tile, g->lossy, g->mu_array, false, s);
+    };
+    auto set_forward_sources = [&]() {
+        a.nsrc = nsrc;
+        for (int q = 0; q < nsrc; ++q) a.src[q] = {src[q].axis, src[q].i, src[q].j, src[q].k};
+        a.amp = (const double *)g->amp.p;
+        a.amp_base = 0;
+        a.amp_len = N;
+    };
+
+    // forward pass with checkpoints and the probe record
+    set_forward_sources();
+    a.nprb = nprb;
+    for (int q = 0; q < nprb; ++q) a.prb[q] = {prb[q].axis, prb[q].i, prb[q].j, prb[q].k};
+    a.mem = mdev;
+    for (long long n = 0; n < N; ++n) {
+        if (n % C == 0)
+            FIT_CHECK(cudaMemcpyAsync(ckpt + (size_t)(n / C) * n6, ring + (size_t)(n & 1) * n6, n6 * sizeof(T),
+                                      cudaMemcpyDeviceToDevice, s));
+        a.it = (int)n;
+        a.parity = (int)(n & 1);
+        FIT_CHECK(step(ring_maps));
+    }
+    a.nprb = 0;
+    double *Jdev = (double *)g->scalar.p;
+    FIT_CHECK(probe_functional(prb, nprb, g->d, aprobe, N, Jdev, s));
+    // adjoint state at N and the adjoint sources
+    FIT_CHECK(adjoint_init<T>(prb, nprb, g->d, aprobe + (size_t)(N - 1) * nprb, (const T *)g->coef.p, lam, g->pitch,
+                              g->ny, ncp, s));
+    FIT_CHECK(adjoint_sources(prb, nprb, g->d, aprobe, N, aamp, s));
+    g->stats.kernel_launches += 3;
+    const double K[3] = {-kEps0 * (g->d[1] * g->d[2] / g->d[0]) / dt, -kEps0 * (g->d[2] * g->d[0] / g->d[1]) / dt,
+                         -kEps0 * (g->d[0] * g->d[1] / g->d[2]) / dt};
+
+    for (long long sg = nseg - 1; sg >= 0; --sg) {
+        const long long A = sg * C, B = std::min<long long>(A + C, N);
+        FIT_CHECK(cudaMemcpyAsync(ring, ckpt + (size_t)sg * n6, n6 * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        set_forward_sources();
+        for (long long q = 0; q < B - A; ++q) {   // ring slot q -> q+1: step A+q
+            a.mem = mdev + 1 + q;
+            a.it = (int)A;
+            a.parity = 0;
+            FIT_CHECK(step(ring_maps));
+        }
+        // adjoint: probe edges are the sources
+        a.nsrc = nprb;
+        for (int q = 0; q < nprb; ++q) a.src[q] = {prb[q].axis, prb[q].i, prb[q].j, prb[q].k};
+        a.amp = aamp;
+        a.amp_base = 0;
+        a.amp_len = N;
+        a.mem = mdev + C + 1;
+        for (long long n = B - 1; n >= A; --n) {
+            const long long t = N - 1 - n;
+            a.it = (int)t;
+            a.parity = (int)(t & 1);
+            FIT_CHECK(step(lam_maps));
+            const T *mu_in = lam + (size_t)(t & 1) * n6;
+            if (fp32_blocks) {
+                FIT_CHECK(grad_accumulate_block(ncp, (const float *)mu_in, (const float *)(ring + (size_t)(n + 1 - A) * n6),
+                                                (const float *)(ring + (size_t)(n - A) * n6), K, (float *)g->gblk.p, s));
+                g->stats.kernel_launches += 1;
+                if ((t + 1) % kGradBlock == 0 || t == N - 1) {
+                    FIT_CHECK(grad_flush(ncp, (float *)g->gblk.p, gacc, s));
+                    g->stats.kernel_launches += 1;
+                }
+            } else {
+                FIT_CHECK(grad_accumulate<T>(ncp, mu_in, ring + (size_t)(n + 1 - A) * n6, ring + (size_t)(n - A) * n6,
+                                             K, gacc, s));
+                g->stats.kernel_launches += 1;
+            }
+        }
+    }
+    // per-cell gradient and J
+    double *gout = grad_out;
+    const bool grad_host = grad_out && !is_device(grad_out);
+    if (grad_host || !grad_out) {
+        if ((rc = ensure(g->grad_ws, sizeof(double) * (size_t)g->ncell))) return rc;
+        gout = (double *)g->grad_ws.p;
+    }
+    FIT_CHECK(grad_scatter(g->nx, g->ny, g->nz, g->pitch, ncp, gacc, gout, s));
+    g->stats.kernel_launches += 1;
+    if (grad_host)
+        FIT_CHECK(cudaMemcpyAsync(grad_out, gout, sizeof(double) * (size_t)g->ncell, cudaMemcpyDeviceToHost, s));
+    if (J_out) FIT_CHECK(cudaMemcpyAsync(J_out, Jdev, sizeof(double), kind_from_dev(J_out), s));
+    const bool host_out = grad_host || (J_out && !is_device(J_out));
+    return finish(g, s, host_out);
+}
+
+}  // namespace
+
+extern "C" {
+
+int fit_adjoint_grad(fit_grid *g, double dt, long nsteps, const fit_source *src, int nsrc, const fit_probe *prb,
+                     int nprb, int ckpt_every, double *J_out, double *grad_eps_r, const fit_run_opts *opts,
+                     void *stream) {
+    if (!g || nsteps < 1 || ckpt_every < 0) return FIT_ERR_ARG;
+    int rc;
+    if ((rc = check_dt(g, dt, opts))) return rc;
+    if ((rc = check_sources_probes(g, src, nsrc, prb, nprb))) return rc;
+    if (opts && (opts->sigma_scheme < 0 || opts->sigma_scheme > 1)) return FIT_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (g->graded) return FIT_ERR_UNSUPPORTED;
+    if (g->prec == 64)
+        return adjoint_impl<double>(g, dt, nsteps, src, nsrc, prb, nprb, ckpt_every, J_out, grad_eps_r, opts, s);
+    if (g->prec == 48 || g->graded) return FIT_ERR_UNSUPPORTED;
+    return adjoint_impl<float>(g, dt, nsteps, src, nsrc, prb, nprb, ckpt_every, J_out, grad_eps_r, opts, s);
+}
+
+}  // extern "C"
