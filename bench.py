@@ -727,7 +727,24 @@ def rk_report(args):
             rows.append({"tol": tol, "k": k, "dt_cfl": dtc, "beta_times_dt_cfl_over_2": u, "leapfrog_steps": n_lf,
                          "leja_q": q, "leja_m": m, "leja_applications": n_leja, "R": n_leja / n_lf,
                          "R_paper_count": n_leja / (2 * n_lf)})
-    print(json.dumps({"study": "R(k), 2-D wave grid, central element d/k", "T": T, "rows": rows}), flush=True)
+    # the uniform-mesh figure: cost against n_x and n_t at the paper's tolerance 1e-2.  Leapfrog
+    # takes max(n_t, T/dt_CFL) steps (the CFL limit caps the step); Leja's cost does not
+    # depend on n_t (dense output), only on beta T
+    uni = []
+    for nxy in (20, 40, 60, 80, 100, 120):
+        w = W.wave2d(n_xy=nxy)
+        g = fitgb.fit_grid_create(w.dims, w.spacing, w.eps_r, None, None, 64)
+        dtc = fitgb.fit_cfl_dt(g)
+        beta = fitgb.fit_spectral_bound(g)
+        fitgb.fit_grid_destroy(g)
+        for nt in (200, 500, 800):
+            dt = T / nt
+            n_lf = nt if dt <= dtc else int(np.ceil(T / dtc))
+            dt_out = T / n_lf
+            q, m = fitgb.fit_expo_plan("leja", dt_out * beta / 2, 1e-2, 64)
+            uni.append({"n_x": nxy, "n_t": nt, "leapfrog_steps": n_lf, "leja_applications": m * int(np.ceil(n_lf / q))})
+    print(json.dumps({"study": "R(k), 2-D wave grid, central element d/k", "T": T, "rows": rows,
+                      "uniform_mesh_cost": uni}), flush=True)
 
 
 def adjoint_report(args):
