@@ -74,6 +74,23 @@ def test_batched_equals_per_problem_runs():
     assert_same(run_problems(ws, batched=True, opts=fitgb.make_opts(tile_x=64, tile_y=4, tile_z=7)), ref)
 
 
+def test_batched_many_items_per_cta():
+    """Enough work items (2000 to 4400) that every persistent CTA takes several,
+    with short z chunks whose plane counts are not multiples of the ring
+    depth: the planes of the next item, prefetched into the ring while the
+    current one finishes, land in the right stages.  Bitwise equal to the
+    problems run one by one."""
+    shapes = [(96, 80, 60), (70, 90, 44), (100, 33, 51)]
+    ws = [W.small_random(dims=d, nsteps=24 + 5 * n, K=4, seed=300 + n, lossy=(n == 1), mu=(n == 2))
+          for n, d in enumerate(shapes)]
+    ref = run_problems(ws, batched=False)
+    assert_same(run_problems(ws, batched=True, opts=fitgb.make_opts(tile_x=32, tile_y=8, tile_z=6)), ref)
+    assert_same(run_problems(ws, batched=True, opts=fitgb.make_opts(tile_x=64, tile_y=4, tile_z=5, stages=3)),
+                ref)
+    assert_same(run_problems(ws, batched=True, opts=fitgb.make_opts(tile_x=32, tile_y=8, tile_z=9, stages=3,
+                                                                    use_graph=1)), ref)
+
+
 def test_batched_with_an_fp64_grid_and_oracle():
     ws = make_batch()[:3]
     precisions = [32, 64, 32]
