@@ -79,6 +79,8 @@ def _load():
         lib.oracle_paraexp.argtypes = [ctypes.POINTER(_Grid), I, P, P, I, P, I, P, P, P, P, P]
         lib.oracle_adjoint.restype = I
         lib.oracle_adjoint.argtypes = [ctypes.POINTER(_Grid), P, P, I, L, L, P, I, P, I, P, P]
+        lib.oracle_adjoint_graded.restype = I
+        lib.oracle_adjoint_graded.argtypes = [ctypes.POINTER(_Grid), P, P, P, P, P, I, L, L, P, I, P, I, P, P]
         lib.oracle_cfl_dt_graded.restype = D
         lib.oracle_cfl_dt_graded.argtypes = [I, I, I, P, P, P, P, P]
         lib.oracle_coeffs_graded.restype = I
@@ -259,16 +261,23 @@ class OracleGrid:
         return best, oe, oh
 
     def adjoint(self, nsteps, sources=(), probes=(), step0=0):
-        """J = sum_n sum_p (e_p^n/L_p)^2 and dJ/d eps_r per cell (shape (nz, ny, nx))."""
-        if self.graded is not None:
-            raise NotImplementedError("the adjoint oracle covers uniform grids")
+        """J = sum_n sum_p (e_p^n/L_p)^2 and dJ/d eps_r per cell (shape (nz, ny, nx)).
+        L_p is the probe edge's length (on a graded grid the size of the cell
+        it runs through along its axis)."""
         src, prb = _structs(sources, probes)
         J = np.zeros(1)
         g = np.zeros((self.nz, self.ny, self.nx))
-        rc = _load().oracle_adjoint(ctypes.byref(self._g), _ptr(self.eps_r), _ptr(self.sigma),
-                                    self.sigma_scheme, int(nsteps), int(step0),
-                                    ctypes.cast(src, ctypes.c_void_p), len(sources),
-                                    ctypes.cast(prb, ctypes.c_void_p), len(probes), _ptr(J), _ptr(g))
+        if self.graded is not None:
+            rc = _load().oracle_adjoint_graded(ctypes.byref(self._g), *(_ptr(a) for a in self.graded),
+                                               _ptr(self.eps_r), _ptr(self.sigma), self.sigma_scheme,
+                                               int(nsteps), int(step0), ctypes.cast(src, ctypes.c_void_p),
+                                               len(sources), ctypes.cast(prb, ctypes.c_void_p), len(probes),
+                                               _ptr(J), _ptr(g))
+        else:
+            rc = _load().oracle_adjoint(ctypes.byref(self._g), _ptr(self.eps_r), _ptr(self.sigma),
+                                        self.sigma_scheme, int(nsteps), int(step0),
+                                        ctypes.cast(src, ctypes.c_void_p), len(sources),
+                                        ctypes.cast(prb, ctypes.c_void_p), len(probes), _ptr(J), _ptr(g))
         if rc:
             raise ValueError(f"oracle_adjoint failed ({rc})")
         return float(J[0]), g

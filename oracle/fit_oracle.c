@@ -394,6 +394,49 @@ done:
     return rc;
 }
 
+/* length of a probe's edge: the grid step along its axis, or on a graded */
+/* grid the size of the cell the edge runs through                          */
+static double probe_len(const or_grid *g, const double *const *ds, const or_probe *p) {
+    if (!ds) return g->d[p->axis];
+    const int q[3] = {p->i, p->j, p->k};
+    return ds[p->axis][q[p->axis]];
+}
+
+/* graded chain rule of one free edge (a, q) at offset p: adds             */
+/* w * (gca dca/dE + gcb dcb/dE) to each of its four cells (see            */
+/* oracle_adjoint_graded)                                                   */
+static void graded_chain(const or_grid *g, const double *const *ds, const float *eps_r, const float *sigma,
+                         int sigma_scheme, int a, const int q[3], long p, double gca, double gcb,
+                         double *grad) {
+    int nx = g->nx, ny = g->ny;
+    int b = (a + 1) % 3, c = (a + 2) % 3;
+    double E = 0.0, S = 0.0, w[4];
+    long cells[4];
+    int nc = 0;
+    for (int sb = 0; sb < 2; ++sb)
+        for (int sc = 0; sc < 2; ++sc) {
+            int r[3] = {q[0], q[1], q[2]};
+            r[b] -= sb;
+            r[c] -= sc;
+            long cc = cidx(nx, ny, r[0], r[1], r[2]);
+            w[nc] = ds[b][r[b]] * ds[c][r[c]] / 4.0;
+            E += (double)eps_r[cc] * w[nc];
+            S += (sigma ? (double)sigma[cc] : 0.0) * w[nc];
+            cells[nc++] = cc;
+        }
+    double s = g->dt * S / (2.0 * OR_EPS0);
+    double dca, dcb;
+    if (sigma_scheme == 0) {
+        dca = 2.0 * s / ((E + s) * (E + s));
+        dcb = -g->cb[p] / (E + s);
+    } else {
+        dca = 2.0 * s / (E * E);
+        dcb = -g->cb[p] / E;
+    }
+    double dJ = gca * dca + gcb * dcb;
+    for (int t = 0; t < 4; ++t) grad[cells[t]] += w[t] * dJ;
+}
+
 /* ------------------------------------------------------------------ */
 /* Adjoint gradient of the probe functional                              */
 /*   J = sum_{n=1..N} sum_p (e_p^n / L_p)^2      (L_p: probe edge length)  */
@@ -413,9 +456,11 @@ done:
 /* grad: nx*ny*nz doubles.  The coefficients in g are used as given (they */
 /* may be float-rounded); the derivative is that of the unrounded map.    */
 /* ------------------------------------------------------------------ */
-int oracle_adjoint(const or_grid *g, const float *eps_r, const float *sigma, int sigma_scheme,
-                   long nsteps, long step0, const or_source *src, int nsrc,
-                   const or_probe *prb, int nprb, double *J_out, double *grad) {
+/* ds: NULL on a uniform grid, else the per-cell sizes {dx, dy, dz} of a    */
+/* graded grid (the chain rule of oracle_adjoint_graded below).            */
+static int adjoint_core(const or_grid *g, const double *const *ds, const float *eps_r, const float *sigma,
+                        int sigma_scheme, long nsteps, long step0, const or_source *src, int nsrc,
+                        const or_probe *prb, int nprb, double *J_out, double *grad) {
     int nx = g->nx, ny = g->ny, nz = g->nz;
     int n[3] = {nx, ny, nz};
     long Np = np_of(g);
@@ -448,7 +493,7 @@ int oracle_adjoint(const or_grid *g, const float *eps_r, const float *sigma, int
             memcpy(H + (size_t)st * S, h, sizeof(double) * S);
             memcpy(E + (size_t)(st + 1) * S, e, sizeof(double) * S);
             for (int p = 0; p < nprb; ++p) {
-                double L = g->d[prb[p].axis];
+                double L = probe_len(g, ds, &prb[p]);
                 double v = e[(long)prb[p].axis * Np + pidx(nx, ny, prb[p].i, prb[p].j, prb[p].k)] / L;
                 J += v * v;
             }
@@ -458,7 +503,7 @@ int oracle_adjoint(const or_grid *g, const float *eps_r, const float *sigma, int
 
     /* lam_e^N = dJ/de^N */
     for (int p = 0; p < nprb; ++p) {
-        double L = g->d[prb[p].axis];
+        double L = probe_len(g, ds, &prb[p]);
         long t = (long)prb[p].axis * Np + pidx(nx, ny, prb[p].i, prb[p].j, prb[p].k);
         le[t] += 2.0 * E[(size_t)nsteps * S + t] / (L * L);
     }
@@ -507,7 +552,7 @@ int oracle_adjoint(const or_grid *g, const float *eps_r, const float *sigma, int
                     }
         if (st >= 1)
             for (int p = 0; p < nprb; ++p) {
-                double L = g->d[prb[p].axis];
+                double L = probe_len(g, ds, &prb[p]);
                 long t = (long)prb[p].axis * Np + pidx(nx, ny, prb[p].i, prb[p].j, prb[p].k);
                 le[t] += 2.0 * en[t] / (L * L);
             }
@@ -536,6 +581,10 @@ int oracle_adjoint(const or_grid *g, const float *eps_r, const float *sigma, int
                             esum += (double)eps_r[cc];
                             ssum += sigma ? (double)sigma[cc] : 0.0;
                         }
+                    if (ds) {
+                        graded_chain(g, ds, eps_r, sigma, sigma_scheme, a, q, p, gca[p], gcb[p], grad);
+                        continue;
+                    }
                     double ebar = esum / 4.0, sbar = ssum / 4.0;
                     double s = g->dt * sbar / (2.0 * OR_EPS0);
                     double dca, dcb;
@@ -553,6 +602,34 @@ int oracle_adjoint(const or_grid *g, const float *eps_r, const float *sigma, int
 done:
     free(E); free(H); free(le); free(lh); free(tmp); free(gca); free(gcb); free(e); free(h);
     return rc;
+}
+
+int oracle_adjoint(const or_grid *g, const float *eps_r, const float *sigma, int sigma_scheme,
+                   long nsteps, long step0, const or_source *src, int nsrc,
+                   const or_probe *prb, int nprb, double *J_out, double *grad) {
+    return adjoint_core(g, NULL, eps_r, sigma, sigma_scheme, nsteps, step0, src, nsrc, prb, nprb, J_out, grad);
+}
+
+/* ------------------------------------------------------------------ */
+/* The adjoint gradient on a graded grid (g built by oracle_coeffs_graded */
+/* from the same sizes).  The reverse sweep is the one above.  J uses the */
+/* probe edge's own length, d_a at its index along a.  The chain rule      */
+/* follows the graded material matrices: with the weight                   */
+/* w = d_b d_c / 4 of each of the four cells around an edge (the part of   */
+/* the dual facet inside it), E = sum w eps_r, S = sum w sigma and         */
+/* s = dt S / (2 eps0), the coefficients are                               */
+/*   scheme 0: ca = (E - s)/(E + s), cb = dt L / (eps0 (E + s))            */
+/*   scheme 1: ca = 1 - 2 s/E,       cb = dt L / (eps0 E)                  */
+/* so dca/dE = 2s/(E+s)^2, dcb/dE = -cb/(E+s) (scheme 1: 2s/E^2, -cb/E)    */
+/* and dE/deps_r(cell) = w of that cell.                                   */
+/* ------------------------------------------------------------------ */
+int oracle_adjoint_graded(const or_grid *g, const double *dx, const double *dy, const double *dz,
+                          const float *eps_r, const float *sigma, int sigma_scheme,
+                          long nsteps, long step0, const or_source *src, int nsrc,
+                          const or_probe *prb, int nprb, double *J_out, double *grad) {
+    const double *ds[3] = {dx, dy, dz};
+    if (!dx || !dy || !dz) return -1;
+    return adjoint_core(g, ds, eps_r, sigma, sigma_scheme, nsteps, step0, src, nsrc, prb, nprb, J_out, grad);
 }
 
 /* Physical constants as used above, exported so a caller can state them. */
