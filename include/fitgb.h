@@ -198,7 +198,7 @@ int fit_grid_create(int nx, int ny, int nz, double dx, double dy, double dz,
  * fit_cfl_dt returns eq. (cfl) with each cell's own sizes.  The exponential
  * propagators interpolate on i[-beta, beta] with beta = ||A||_1 (the largest
  * absolute row sum of A, a bound on ||A||_2), since eq. (cfl) is only an
- * estimate on such grids.  fit_adjoint_grad returns FIT_ERR_UNSUPPORTED. */
+ * estimate on such grids. */
 int fit_grid_create_graded(int nx, int ny, int nz, const double *dx, const double *dy, const double *dz,
                            const float *eps_r, const float *mu_r, const float *sigma,
                            int precision, unsigned flags, fit_grid **out);
@@ -349,7 +349,10 @@ int paraexp_run_batched(const fit_paraexp_problem *probs, int nprobs,
  * per-cell eps_r.  The reverse sweep transposes the leapfrog step (derived
  * from Sec. II-A); states are recomputed from checkpoints of (e, h) taken
  * every ckpt_every steps (0 = about sqrt(N)).  J_out: 1 double; grad_eps_r:
- * nx*ny*nz doubles (dJ/d eps_r per cell); both may be host or device. */
+ * nx*ny*nz doubles (dJ/d eps_r per cell); both may be host or device.
+ * On a graded grid L_p is the size of the cell the probe edge runs through
+ * along its axis, and each cell's share of an edge's M_eps is its own
+ * d_b d_c / 4 (the material matrices of fit_grid_create_graded). */
 int fit_adjoint_grad(fit_grid *g, double dt, long nsteps,
                      const fit_source *src, int nsrc, const fit_probe *prb, int nprb,
                      int ckpt_every, double *J_out, double *grad_eps_r,

@@ -19,6 +19,12 @@
 // and d eps_bar / d eps_r(cell) = 1/4 for each of the four cells around the
 // edge.  Edges in a PEC wall have cb = 0, so mu and their gradient vanish by
 // themselves.
+//
+// Graded grids: M_eps = (eps0 / d_a) sum over the four cells of
+// eps_r d_b d_c / 4, so each cell's weight is its own d_b d_c / 4 and the
+// edge length d_a is that cell's size along a as well.  The accumulation then
+// runs with K = -eps0 / dt on every axis, and the scatter multiplies the four
+// a-edges of a cell by d_b d_c / d_a of that cell (the 1/4 stays).
 #include "internal.h"
 
 namespace fitgb {
@@ -97,8 +103,11 @@ __global__ void grad_flush_kernel(long long n3, float *gb, double *g) {
     }
 }
 
-// dJ/d eps_r(cell) = 1/4 sum over the 12 edges around the cell of g_edge
-__global__ void scatter_kernel(int nx, int ny, int nz, int pitch, long long ncp, const double *g, double *grad) {
+// dJ/d eps_r(cell) = 1/4 sum over the 12 edges around the cell of g_edge;
+// spc (graded grids; null on uniform ones): dx[nx], dy[ny], dz[nz] in a row,
+// the edges along a weighted by the cell's d_b d_c / d_a
+__global__ void scatter_kernel(int nx, int ny, int nz, int pitch, long long ncp, const double *g, const double *spc,
+                               double *grad) {
     const long long ncell = (long long)nx * ny * nz;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
          c += (long long)gridDim.x * blockDim.x) {
@@ -109,6 +118,18 @@ __global__ void scatter_kernel(int nx, int ny, int nz, int pitch, long long ncp,
             if (ii >= nx || jj >= ny || kk >= nz) return 0.0;   // edge in a wall: no degree of freedom
             return g[(long long)a * ncp + ((long long)kk * ny + jj) * pitch + ii];
         };
+        if (spc) {
+            double sx = 0.0, sy = 0.0, sz = 0.0;
+            for (int u = 0; u < 2; ++u)
+                for (int v = 0; v < 2; ++v) {
+                    sx += at(0, i, j + u, k + v);
+                    sy += at(1, i + u, j, k + v);
+                    sz += at(2, i + u, j + v, k);
+                }
+            const double dx = spc[i], dy = spc[nx + j], dz = spc[nx + ny + k];
+            grad[c] = 0.25 * (sx * (dy * dz / dx) + sy * (dz * dx / dy) + sz * (dx * dy / dz));
+            continue;
+        }
         double s = 0.0;
         for (int u = 0; u < 2; ++u)
             for (int v = 0; v < 2; ++v) {
@@ -139,12 +160,13 @@ __global__ void functional_kernel(ProbeList pl, const double *probe, long long N
     }
 }
 
-ProbeList make_list(const fit_probe *prb, int nprb, const double d[3]) {
+// plen: the length of each probe's edge (host, nprb values)
+ProbeList make_list(const fit_probe *prb, int nprb, const double *plen) {
     ProbeList pl;
     pl.n = nprb;
     for (int q = 0; q < nprb && q < kMaxSrc; ++q) {
         pl.p[q] = {prb[q].axis, prb[q].i, prb[q].j, prb[q].k};
-        const double L = d[prb[q].axis];
+        const double L = plen[q];
         pl.inv_l2[q] = 1.0 / (L * L);
     }
     return pl;
@@ -153,15 +175,15 @@ ProbeList make_list(const fit_probe *prb, int nprb, const double d[3]) {
 }  // namespace
 
 template <typename T>
-cudaError_t adjoint_init(const fit_probe *prb, int nprb, const double d[3], const double *probe_last, const T *cb,
+cudaError_t adjoint_init(const fit_probe *prb, int nprb, const double *plen, const double *probe_last, const T *cb,
                          T *mu, int pitch, int ny, long long ncp, cudaStream_t s) {
-    adjoint_init_kernel<T><<<1, 32, 0, s>>>(make_list(prb, nprb, d), probe_last, cb, mu, pitch, ny, ncp);
+    adjoint_init_kernel<T><<<1, 32, 0, s>>>(make_list(prb, nprb, plen), probe_last, cb, mu, pitch, ny, ncp);
     return cudaGetLastError();
 }
 
-cudaError_t adjoint_sources(const fit_probe *prb, int nprb, const double d[3], const double *probe, long long N,
+cudaError_t adjoint_sources(const fit_probe *prb, int nprb, const double *plen, const double *probe, long long N,
                             double *amp, cudaStream_t s) {
-    adjoint_amp_kernel<<<grid_for(N * nprb), kThreads, 0, s>>>(make_list(prb, nprb, d), probe, N, amp);
+    adjoint_amp_kernel<<<grid_for(N * nprb), kThreads, 0, s>>>(make_list(prb, nprb, plen), probe, N, amp);
     return cudaGetLastError();
 }
 
@@ -184,15 +206,15 @@ cudaError_t grad_flush(long long ncp, float *gb, double *g, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t grad_scatter(int nx, int ny, int nz, int pitch, long long ncp, const double *g, double *grad,
-                         cudaStream_t s) {
-    scatter_kernel<<<grid_for((long long)nx * ny * nz), kThreads, 0, s>>>(nx, ny, nz, pitch, ncp, g, grad);
+cudaError_t grad_scatter(int nx, int ny, int nz, int pitch, long long ncp, const double *g, const double *spc,
+                         double *grad, cudaStream_t s) {
+    scatter_kernel<<<grid_for((long long)nx * ny * nz), kThreads, 0, s>>>(nx, ny, nz, pitch, ncp, g, spc, grad);
     return cudaGetLastError();
 }
 
-cudaError_t probe_functional(const fit_probe *prb, int nprb, const double d[3], const double *probe, long long N,
+cudaError_t probe_functional(const fit_probe *prb, int nprb, const double *plen, const double *probe, long long N,
                              double *J, cudaStream_t s) {
-    functional_kernel<<<1, kThreads, 0, s>>>(make_list(prb, nprb, d), probe, N, J);
+    functional_kernel<<<1, kThreads, 0, s>>>(make_list(prb, nprb, plen), probe, N, J);
     return cudaGetLastError();
 }
 

@@ -136,15 +136,25 @@ int adjoint_impl(fit_grid *g, double dt, long long N, const fit_source *src, int
         FIT_CHECK(step(ring_maps));
     }
     a.nprb = 0;
+    // each probe edge's length: the grid step, or on a graded grid the size of
+    // the cell the edge runs through along its axis
+    double plen[kMaxSrc];
+    for (int q = 0; q < nprb; ++q) {
+        const int ax = prb[q].axis, idx[3] = {prb[q].i, prb[q].j, prb[q].k};
+        const size_t off = ax == 0 ? 0 : (ax == 1 ? (size_t)g->nx : (size_t)g->nx + g->ny);
+        plen[q] = g->graded ? g->spc_host[off + idx[ax]] : g->d[ax];
+    }
     double *Jdev = (double *)g->scalar.p;
-    FIT_CHECK(probe_functional(prb, nprb, g->d, aprobe, N, Jdev, s));
+    FIT_CHECK(probe_functional(prb, nprb, plen, aprobe, N, Jdev, s));
     // adjoint state at N and the adjoint sources
-    FIT_CHECK(adjoint_init<T>(prb, nprb, g->d, aprobe + (size_t)(N - 1) * nprb, (const T *)g->coef.p, lam, g->pitch,
+    FIT_CHECK(adjoint_init<T>(prb, nprb, plen, aprobe + (size_t)(N - 1) * nprb, (const T *)g->coef.p, lam, g->pitch,
                               g->ny, ncp, s));
-    FIT_CHECK(adjoint_sources(prb, nprb, g->d, aprobe, N, aamp, s));
+    FIT_CHECK(adjoint_sources(prb, nprb, plen, aprobe, N, aamp, s));
     g->stats.kernel_launches += 3;
-    const double K[3] = {-kEps0 * (g->d[1] * g->d[2] / g->d[0]) / dt, -kEps0 * (g->d[2] * g->d[0] / g->d[1]) / dt,
-                         -kEps0 * (g->d[0] * g->d[1] / g->d[2]) / dt};
+    // -eps0 A_a / (L_a dt) per axis; on a graded grid the geometry goes into the scatter
+    const double K[3] = {g->graded ? -kEps0 / dt : -kEps0 * (g->d[1] * g->d[2] / g->d[0]) / dt,
+                         g->graded ? -kEps0 / dt : -kEps0 * (g->d[2] * g->d[0] / g->d[1]) / dt,
+                         g->graded ? -kEps0 / dt : -kEps0 * (g->d[0] * g->d[1] / g->d[2]) / dt};
 
     for (long long sg = nseg - 1; sg >= 0; --sg) {
         const long long A = sg * C, B = std::min<long long>(A + C, N);
@@ -191,7 +201,8 @@ int adjoint_impl(fit_grid *g, double dt, long long N, const fit_source *src, int
         if ((rc = ensure(g->grad_ws, sizeof(double) * (size_t)g->ncell))) return rc;
         gout = (double *)g->grad_ws.p;
     }
-    FIT_CHECK(grad_scatter(g->nx, g->ny, g->nz, g->pitch, ncp, gacc, gout, s));
+    FIT_CHECK(grad_scatter(g->nx, g->ny, g->nz, g->pitch, ncp, gacc, g->graded ? (const double *)g->spc.p : nullptr,
+                           gout, s));
     g->stats.kernel_launches += 1;
     if (grad_host)
         FIT_CHECK(cudaMemcpyAsync(grad_out, gout, sizeof(double) * (size_t)g->ncell, cudaMemcpyDeviceToHost, s));
@@ -213,10 +224,9 @@ int fit_adjoint_grad(fit_grid *g, double dt, long nsteps, const fit_source *src,
     if ((rc = check_sources_probes(g, src, nsrc, prb, nprb))) return rc;
     if (opts && (opts->sigma_scheme < 0 || opts->sigma_scheme > 1)) return FIT_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    if (g->graded) return FIT_ERR_UNSUPPORTED;
     if (g->prec == 64)
         return adjoint_impl<double>(g, dt, nsteps, src, nsrc, prb, nprb, ckpt_every, J_out, grad_eps_r, opts, s);
-    if (g->prec == 48 || g->graded) return FIT_ERR_UNSUPPORTED;
+    if (g->prec == 48) return FIT_ERR_UNSUPPORTED;
     return adjoint_impl<float>(g, dt, nsteps, src, nsrc, prb, nprb, ckpt_every, J_out, grad_eps_r, opts, s);
 }
 

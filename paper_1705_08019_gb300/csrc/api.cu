@@ -567,6 +567,7 @@ int fit_grid_create_graded(int nx, int ny, int nz, const double *dx, const doubl
         return FIT_ERR_OOM;
     }
     g->graded = true;
+    g->spc_host = spc;
     g->mu_array = true;   // ch varies per face
     if (graded_cfl_and_bound(nx, ny, nz, (const double *)g->spc.p, g->eps, g->mu, g->scratch.p, &g->cfl_graded,
                              &g->rowsum, 0) != cudaSuccess) {

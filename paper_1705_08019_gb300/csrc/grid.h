@@ -33,6 +33,7 @@ struct fit_grid {
     // graded grids: per-axis cell sizes on the device, eq. (cfl) with local sizes, ||A||_1
     bool graded = false;
     Buf spc;
+    std::vector<double> spc_host;   // the same sizes on the host
     double cfl_graded = 0.0, rowsum = 0.0;
     // coefficient cache
     bool c_valid = false, c_has_energy = false;

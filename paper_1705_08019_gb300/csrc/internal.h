@@ -268,11 +268,11 @@ bool encode_window_map(CUtensorMap *out, int elem_bytes, int nx, int ny, int nz,
 // out[t] += sum_m pm[m*stride + t], members in order
 cudaError_t add_members(int nmem, long long len, const double *pm, long long stride, double *out, cudaStream_t s);
 
-// adjoint.cu
+// adjoint.cu (plen: host array of each probe edge's length)
 template <typename T>
-cudaError_t adjoint_init(const fit_probe *prb, int nprb, const double d[3], const double *probe_last, const T *cb,
+cudaError_t adjoint_init(const fit_probe *prb, int nprb, const double *plen, const double *probe_last, const T *cb,
                          T *mu, int pitch, int ny, long long ncp, cudaStream_t s);
-cudaError_t adjoint_sources(const fit_probe *prb, int nprb, const double d[3], const double *probe, long long N,
+cudaError_t adjoint_sources(const fit_probe *prb, int nprb, const double *plen, const double *probe, long long N,
                             double *amp, cudaStream_t s);
 template <typename T>
 cudaError_t grad_accumulate(long long ncp, const T *mu, const T *e1, const T *e0, const double k[3], double *g,
@@ -281,9 +281,10 @@ cudaError_t grad_accumulate(long long ncp, const T *mu, const T *e1, const T *e0
 cudaError_t grad_accumulate_block(long long ncp, const float *mu, const float *e1, const float *e0, const double k[3],
                                   float *gb, cudaStream_t s);
 cudaError_t grad_flush(long long ncp, float *gb, double *g, cudaStream_t s);
-cudaError_t grad_scatter(int nx, int ny, int nz, int pitch, long long ncp, const double *g, double *grad,
-                         cudaStream_t s);
-cudaError_t probe_functional(const fit_probe *prb, int nprb, const double d[3], const double *probe, long long N,
+// spc: device dx[nx], dy[ny], dz[nz] of a graded grid, or null
+cudaError_t grad_scatter(int nx, int ny, int nz, int pitch, long long ncp, const double *g, const double *spc,
+                         double *grad, cudaStream_t s);
+cudaError_t probe_functional(const fit_probe *prb, int nprb, const double *plen, const double *probe, long long N,
                              double *J, cudaStream_t s);
 
 }  // namespace fitgb

@@ -1,6 +1,6 @@
 """Graded (tensor-product) grids on the GPU against the oracle: leapfrog,
-ParaExp with leapfrog and with Leja homogeneous problems, the CFL estimate
-and the spectral bound.  Tolerances as in test_gpu_parity.py (FP64 1e-11,
+ParaExp with leapfrog and with Leja homogeneous problems, the CFL estimate,
+the spectral bound and the adjoint gradient.  Tolerances as in test_gpu_parity.py (FP64 1e-11,
 FP32 from the oracle's store32 model) and test_gpu_expo.py (1e-10)."""
 import numpy as np
 import pytest
@@ -95,10 +95,32 @@ def test_graded_paraexp_leja_equals_oracle(precision):
     assert relerr(ef, compact(oef)) <= b and relerr(hf, compact(ohf)) <= b
 
 
-def test_graded_adjoint_is_unsupported():
-    w = setup()
-    g = fitgb.Grid(w.dims, w.spacing, w.eps_r, None, w.sigma, 64)
-    with pytest.raises(fitgb.FitError) as ei:
-        g.adjoint(0.9 * g.cfl_dt(), 10, w.sources, w.probes)
-    assert ei.value.status == fitgb.FIT_ERR_UNSUPPORTED
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_graded_adjoint_fp64_equals_oracle(scheme):
+    """dJ/d eps_r on a lossy graded grid with non-uniform mu_r: the GPU's
+    scaled-multiplier sweep with the graded scatter against the oracle's
+    reverse sweep and coefficient chain rule (two independent derivations,
+    the oracle's pinned by finite differences)."""
+    w = setup(dims=(14, 9, 11), seed=9)
+    prbs = w.probes[:3]
+    dt = 0.9 * oracle.cfl_dt(w.dims, w.spacing, w.eps_r, w.mu_r)
+    g = fitgb.Grid(w.dims, w.spacing, w.eps_r, w.mu_r, w.sigma, 64)
+    J, grad = g.adjoint(dt, 120, w.sources, prbs, ckpt_every=13, opts=fitgb.make_opts(sigma_scheme=scheme))
     g.close()
+    og = oracle.OracleGrid(w.dims, w.spacing, w.eps_r, w.mu_r, w.sigma, dt=dt, sigma_scheme=scheme)
+    J_ref, g_ref = og.adjoint(120, w.sources, prbs)
+    assert abs(J - J_ref) <= 1e-11 * abs(J_ref)
+    assert relerr(grad[None], g_ref[None]) <= 1e-9
+
+
+def test_graded_adjoint_fp32_equals_oracle():
+    w = setup(dims=(19, 13, 11), seed=10)
+    prbs = w.probes[:3]
+    dt = 0.9 * oracle.cfl_dt(w.dims, w.spacing, w.eps_r, w.mu_r)
+    g = fitgb.Grid(w.dims, w.spacing, w.eps_r, w.mu_r, w.sigma, 32)
+    J, grad = g.adjoint(dt, 200, w.sources, prbs)
+    g.close()
+    og = oracle.OracleGrid(w.dims, w.spacing, w.eps_r, w.mu_r, w.sigma, dt=dt, round32=True)
+    J_ref, g_ref = og.adjoint(200, w.sources, prbs)
+    assert abs(J - J_ref) <= 1e-4 * abs(J_ref)
+    assert relerr(grad[None], g_ref[None]) <= 1e-3
