@@ -4,14 +4,25 @@
 returns J = sum_{n=1..N} sum_p (e_p^n / L_p)^2 of an FP32 leapfrog run from
 zero state on a grid with per-cell permittivity ``eps_r`` (a float32 CUDA
 tensor of shape (nz, ny, nx)); ``J.backward()`` gives dJ/d eps_r from the
-adjoint sweep of libfitgb (fit_adjoint_grad).  Torch only holds the tensors
+adjoint sweep of libfitgb (fit_adjoint_grad).  ``spacing`` holds three
+steps, or per-cell sizes along an axis for a graded grid; L_p is then the
+size of the cell the probe edge runs through along its axis.  Torch only holds the tensors
 and the stream: the run and its gradient are the library's kernels.
 """
 from __future__ import annotations
 
+import numpy as np
 import torch
 
 from . import fitgb
+
+
+def edge_length(spacing, p):
+    """Length of probe p's edge: the step along its axis, or on a graded axis
+    the size of the cell at the probe's index along it."""
+    a = p["axis"]
+    d = spacing[a]
+    return float(d) if np.ndim(d) == 0 else float(np.asarray(d)[(p["i"], p["j"], p["k"])[a]])
 
 
 class ProbeEnergy(torch.autograd.Function):
@@ -32,7 +43,7 @@ class ProbeEnergy(torch.autograd.Function):
             else:
                 pr = torch.zeros((nsteps, len(probes)), dtype=torch.float64, device=dev)
                 fitgb.fit_leapfrog_run(g.handle, dt, nsteps, 0, sources, probes, pr, stream=stream)
-                L = torch.tensor([spacing[p["axis"]] for p in probes], dtype=torch.float64, device=dev)
+                L = torch.tensor([edge_length(spacing, p) for p in probes], dtype=torch.float64, device=dev)
                 J = ((pr / L) ** 2).sum().reshape(1)
             torch.cuda.synchronize(dev)
         finally:
