@@ -207,3 +207,88 @@ def test_graded_adjoint_with_constant_sizes_equals_uniform():
     Jg, grg = gg.adjoint(40, srcs, prbs)
     assert abs(Jg - Ju) <= 1e-13 * Ju
     assert np.max(np.abs(grg - gru)) <= 1e-12 * np.max(np.abs(gru))
+
+
+def complex_step_J(dims, sizes, eps, sig, dt, scheme, srcs, prbs, N, direction, h=1e-30, spacing=None):
+    """J(eps + i h direction) of an N-step run from zero state, by a dense
+    complex leapfrog over the incidence matrix of tests/dense_fit.py.  The
+    edge coefficients are formed from complex eps with the graded material
+    matrices; Im(J) / h is then the exact directional derivative
+    (complex-step differentiation), independent of the adjoint sweep.
+    `spacing` (default: sizes) is what the oracle grid gets: three scalars
+    make it a uniform grid.  Returns (J real part, directional derivative,
+    (real ca, real cb, oracle grid))."""
+    d = DenseFIT(dims)
+    nx, ny, nz = dims
+    Np = d.Np
+    epsc = eps.astype(np.float64) + 1j * h * direction
+    sigv = np.zeros(eps.shape) if sig is None else sig.astype(np.float64)
+    ca = np.zeros(3 * Np, complex)
+    cb = np.zeros(3 * Np, complex)
+    for r in np.flatnonzero(d.edge_dof):
+        a, p = divmod(int(r), Np)
+        q = (p % (nx + 1), (p // (nx + 1)) % (ny + 1), p // ((nx + 1) * (ny + 1)))
+        b, c = (a + 1) % 3, (a + 2) % 3
+        E = S = 0.0
+        for sb in (0, 1):
+            for sc in (0, 1):
+                cell = list(q)
+                cell[b] -= sb
+                cell[c] -= sc
+                w = sizes[b][cell[b]] * sizes[c][cell[c]] / 4.0
+                E = E + epsc[cell[2], cell[1], cell[0]] * w
+                S = S + sigv[cell[2], cell[1], cell[0]] * w
+        L = sizes[a][q[a]]
+        me, ms = EPS0 * E / L, S / L
+        av = dt * ms / (2.0 * me)
+        if scheme == 0:
+            ca[r], cb[r] = (1.0 - av) / (1.0 + av), dt / (me * (1.0 + av))
+        else:
+            ca[r], cb[r] = 1.0 - 2.0 * av, dt / me
+    og = oracle.OracleGrid(dims, sizes if spacing is None else spacing, eps, None, sig, dt=dt, sigma_scheme=scheme)
+    ch = og.ch.ravel()
+    e = np.zeros(3 * Np, complex)
+    hh = np.zeros(3 * Np, complex)
+    J = 0.0
+    for n in range(N):
+        hh = hh - ch * (d.C @ e)
+        jv = np.zeros(3 * Np)
+        for s in srcs:
+            jv[s["axis"] * Np + d.pidx((s["i"], s["j"], s["k"]))] += oracle.waveform(
+                s["waveform"], s["amp"], s["f0"], s["width"], s["delay"], (n + 0.5) * dt)
+        e = ca * e + cb * (d.C.T @ hh - jv)
+        for pr in prbs:
+            q = (pr["i"], pr["j"], pr["k"])
+            J = J + (e[pr["axis"] * Np + d.pidx(q)] / sizes[pr["axis"]][q[pr["axis"]]]) ** 2
+    return float(J.real), float(J.imag) / h, (ca.real, cb.real, og)
+
+
+@pytest.mark.parametrize("graded,scheme", [(True, 0), (True, 1), (False, 0)])
+def test_adjoint_matches_complex_step_derivatives(graded, scheme):
+    """The oracle's adjoint gradient against exact directional derivatives of
+    J (complex step through a dense complex leapfrog): grad . v = dJ(eps; v)
+    for random directions v and single cells, to 1e-10."""
+    dims = (4, 3, 3)
+    uniform = (1e-3, 1.2e-3, 0.8e-3)
+    sizes = rand_graded(dims, 91, ratio=4.0) if graded else [np.full(n, v) for n, v in zip(dims, uniform)]
+    spacing = sizes if graded else uniform
+    eps, _, sig = rand_materials(dims, 92, lossy=True, mu=False)
+    dt = 0.9 * oracle.cfl_dt(dims, spacing, eps)
+    srcs = [dict(axis=2, i=2, j=1, k=1, waveform=0, amp=1.0, f0=80e9, width=15 * dt, delay=15 * dt)]
+    prbs = [dict(axis=2, i=1, j=2, k=1), dict(axis=0, i=2, j=1, k=2), dict(axis=1, i=3, j=0, k=2)]
+    N = 40
+    rng = np.random.default_rng(93)
+    dirs = [rng.standard_normal(eps.shape) for _ in range(3)]
+    for idx in [(0, 0, 0), (1, 2, 3), (2, 1, 1)]:
+        v = np.zeros(eps.shape)
+        v[idx] = 1.0
+        dirs.append(v)
+    J0, _, (ca, cb, og) = complex_step_J(dims, sizes, eps, sig, dt, scheme, srcs, prbs, N, dirs[0], spacing=spacing)
+    assert (og.graded is not None) == graded
+    # the restated coefficients are the oracle's, so the comparison is about the sweep
+    assert np.max(np.abs(ca - og.ca.ravel())) <= 1e-15 and np.max(np.abs(cb - og.cb.ravel())) <= 1e-15 * np.abs(cb).max()
+    J, grad = og.adjoint(N, srcs, prbs)
+    assert abs(J - J0) <= 1e-12 * J
+    for v in dirs:
+        _, dJ, _ = complex_step_J(dims, sizes, eps, sig, dt, scheme, srcs, prbs, N, v, spacing=spacing)
+        assert abs(float(np.sum(grad * v)) - dJ) <= 1e-10 * np.abs(grad).sum() * np.abs(v).max(), (dJ, np.sum(grad * v))
