@@ -65,7 +65,7 @@ typedef enum {
     FIT_ERR_CUDA = -4,      /* CUDA runtime error                           */
     FIT_ERR_TIMEOUT = -5,   /* a bounded device wait gave up                */
     FIT_ERR_NONFINITE = -6, /* non-finite or non-positive material value    */
-    FIT_ERR_UNSUPPORTED = -7/* valid request this build does not implement  */
+    FIT_ERR_UNSUPPORTED = -7/* valid request the library does not implement */
 } fit_status;
 
 /* Source waveforms i(t) [A] of an edge current. */
