@@ -33,6 +33,9 @@ sys.path.insert(0, ROOT)
 METRIC = "FIT leapfrog Gcell-updates/s (% HBM roofline); batched ParaExp & adjoint vs plain"
 UNIT = "Gcell-updates/s"
 L2_BYTES = 129e6
+# bytes of one state (e and h) per cell, and the name of each field precision
+STATE_BYTES = {32: 24, 40: 36, 48: 48, 64: 48}
+PREC_NAME = {32: "fp32", 40: "fp32 + bf16 residual", 48: "fp32 pairs (compensated)", 64: "fp64"}
 
 
 def parse():
@@ -42,6 +45,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="boxes256")
+    ap.add_argument("--precision", type=int, default=None,
+                    help="field precision of the solve: 32, 40 (FP32 + bfloat16 residual), 48 or 64 "
+                         "[default: the workload's]")
+    ap.add_argument("--nsteps", type=int, default=None, help="override the workload's step count")
+    ap.add_argument("--kernel", type=int, default=0, help="opts.kernel of the solve [0 = the library's default]")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--compare-plain", action="store_true",
@@ -70,12 +78,15 @@ def parse():
     return ap.parse_args()
 
 
-def load_workload(name):
+def load_workload(name, args=None):
     from paper_1705_08019_gb300 import workloads as W
     if name == "batch64":
         return W.cavity_batch()
     if name == "boxes256":
-        return W.boxes256()
+        w = W.boxes256(nsteps=args.nsteps) if args is not None and args.nsteps else W.boxes256()
+        if args is not None and args.precision:
+            w.precision = args.precision
+        return w
     if name == "cavity16":
         return W.cavity16()
     if name == "boxes512":
@@ -89,9 +100,9 @@ def load_workload(name):
 
 def config_of(w, extra=None):
     nx, ny, nz = w.dims
-    state_bytes = 2 * 6 * (4 if w.precision == 32 else 8) * w.ncells * w.K
+    state_bytes = 2 * STATE_BYTES[w.precision] * w.ncells * w.K
     cfg = {"workload": w.name, "cells": f"{nx}x{ny}x{nz}", "nsteps": w.nsteps, "K": w.K,
-           "precision": f"fp{w.precision}", "lossy": w.sigma is not None,
+           "precision": PREC_NAME[w.precision], "lossy": w.sigma is not None,
            "l2": ("inputs larger than L2: %.1f GB of member state" % (state_bytes / 1e9))
            if state_bytes > L2_BYTES else "fits in L2 (small case)",
            "parallelism": "replicas (independent problems per GPU)"}
@@ -131,7 +142,7 @@ def oracle_sample(w, nsteps=4, K=2):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    w = load_workload(args.workload)
+    w = load_workload(args.workload, args)
     for _ in range(args.warmup):
         oracle_sample(w)
     secs, rate, desc = [], None, None
@@ -255,8 +266,7 @@ def run_ours(args, rank, world, local_rank):
     dist = None
     if world > 1:
         import torch.distributed as dist
-    w = load_workload(args.workload)
-    T = torch.float32 if w.precision == 32 else torch.float64
+    w = load_workload(args.workload, args)
     nx, ny, nz = w.dims
     eps_d = torch.from_numpy(w.eps_r).to(dev)
     sig_d = torch.from_numpy(w.sigma).to(dev) if w.sigma is not None else None
@@ -274,7 +284,8 @@ def run_ours(args, rank, world, local_rank):
     def step(profile=True, members_per_pass=0):
         g = fitgb.fit_grid_create(w.dims, w.spacing, eps_d, mu_d, sig_d, w.precision)
         fitgb.paraexp_run(g, dt, w.K, win, w.sources, w.probes, probe_d, ef_d, hf_d,
-                          opts=fitgb.make_opts(profile=int(profile), members_per_pass=members_per_pass),
+                          opts=fitgb.make_opts(profile=int(profile), members_per_pass=members_per_pass,
+                                               kernel=args.kernel),
                           stream=stream)
         st = fitgb.fit_last_stats(g)
         fitgb.fit_grid_destroy(g)
@@ -362,7 +373,7 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32" if w.precision == 32 else "f64", "data": "synthetic",
+                "vs_baseline": None, "dtype": "f64" if w.precision == 64 else "f32", "data": "synthetic",
                 "config": config_of(w), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(sum(s["kernel_launches"] for s in stats)), "clocks": ck}
         line.update(extras)
@@ -392,7 +403,7 @@ def ncu_case(args):
         for g in gs:
             fitgb.fit_grid_destroy(g)
         return
-    w = load_workload(args.workload)
+    w = load_workload(args.workload, args)
     dev = torch.device("cuda", 0)
     eps = torch.from_numpy(w.eps_r).to(dev)
     sig = torch.from_numpy(w.sigma).to(dev) if w.sigma is not None else None
@@ -521,7 +532,7 @@ def accuracy_report(args):
     from paper_1705_08019_gb300 import fitgb
     B.build()
     fitgb.load()
-    w = load_workload(args.workload)
+    w = load_workload(args.workload, args)
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     eps = torch.from_numpy(w.eps_r).to(dev)

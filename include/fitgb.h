@@ -30,9 +30,9 @@
  *   and are not stored.  Entries that are not degrees of freedom (e
  *   tangential to a wall, h normal to a wall) are ignored on input and
  *   returned as zero.
- * Precision: a grid is created for FP32, FP64 or compensated-FP32 fields;
- *   field arrays passed to it (e_io, h_io) are float for FP32 and double
- *   otherwise.  Probe traces,
+ * Precision: a grid is created for FP32, FP64, FP32-with-residual or
+ *   compensated-FP32 fields; field arrays passed to it (e_io, h_io) are float
+ *   for FP32 and double otherwise.  Probe traces,
  *   energies, superposed fields, J and gradients are always double.
  * Pointers: every array argument may be a host or a device pointer; the
  *   library finds out with cudaPointerGetAttributes.  The caller owns all
@@ -104,7 +104,9 @@ typedef struct {
     int profile;                /* 1: time every step launch with CUDA events
                                    on the run's stream (fit_last_stats) [0]   */
     int kernel;                 /* step kernel: 1 shared-memory staging by
-                                   plain loads, 2 TMA pipeline [0 = 2]        */
+                                   plain loads, 2 TMA pipeline; precision 40:
+                                   2 two cells per thread, 3 one cell per
+                                   thread [0 = 2]                             */
     int stages;                 /* TMA ring depth in planes, 3 or 4 (FP32
                                    TMA kernels; 0 = the tile's default)       */
     int debug_wait_limit;       /* test hook: polls before a TMA-kernel wait
@@ -170,13 +172,23 @@ typedef struct {
 
 /* Create a grid and upload its per-cell materials.
  *   eps_r (required), mu_r (NULL = 1), sigma [S/m] (NULL = 0): nx*ny*nz.
- *   precision: 32 (float fields), 64 (double fields), or 48: compensated
- *     FP32 fields, each value an unevaluated sum hi + lo of two floats (about
- *     48 significant bits), advanced in FP32 arithmetic with error-free sums
- *     and products; its field arrays (e_io, h_io, e0, h0) are double.
- *     The compensated mode runs fit_leapfrog_run and paraexp_run (FP64
- *     superposition) with the TMA kernel; fit_adjoint_grad returns
- *     FIT_ERR_UNSUPPORTED for it.
+ *   precision: 32 (float fields), 64 (double fields), 40 or 48:
+ *     40: FP32 fields that carry a residual: each value is hi + lo, hi a
+ *     float and lo the rounding residual of hi stored as a bfloat16 (6 bytes
+ *     per value).  Updates are FP32 arithmetic: the increment is summed into
+ *     hi by a fast two-sum and the residual kept; the curl C e of the
+ *     magnetic update is formed from two same-component differences made
+ *     error-free by two-sums (so a large curl-free part of e cancels
+ *     exactly); products with the coefficients are split by one FMA.  About
+ *     10x smaller field error than 32 for 1.5x its field bytes.
+ *     48: compensated FP32 fields, each value an unevaluated sum hi + lo of
+ *     two floats (about 48 significant bits), advanced in FP32 arithmetic
+ *     with error-free sums and products.
+ *     The field arrays of 40 and 48 (e_io, h_io, e0, h0) are double.  Both
+ *     run fit_leapfrog_run and paraexp_run (FP64 superposition, sum_mode 0)
+ *     with a TMA kernel; fit_adjoint_grad, fit_expo_propagate and the
+ *     exponential homogeneous propagators return FIT_ERR_UNSUPPORTED for
+ *     them, and paraexp_run_batched runs their problems one after another.
  * Material matrices (Sec. II, eq. maxwell_grid3): M_eps on an edge is eps0
  * times the area-weighted mean of eps_r over the four cells around it, times
  * dual area / length; M_sigma likewise; M_mu on a face is mu0 times the
@@ -349,7 +361,9 @@ int paraexp_run_batched(const fit_paraexp_problem *probs, int nprobs,
  * per-cell eps_r.  The reverse sweep transposes the leapfrog step (derived
  * from Sec. II-A); states are recomputed from checkpoints of (e, h) taken
  * every ckpt_every steps (0 = about sqrt(N)).  J_out: 1 double; grad_eps_r:
- * nx*ny*nz doubles (dJ/d eps_r per cell); both may be host or device.
+ * nx*ny*nz doubles (dJ/d eps_r per cell); both may be host or device, and
+ * either may be NULL.  With grad_eps_r NULL only the forward run and J are
+ * computed (no checkpoints, no reverse sweep).
  * On a graded grid L_p is the size of the cell the probe edge runs through
  * along its axis, and each cell's share of an edge's M_eps is its own
  * d_b d_c / 4 (the material matrices of fit_grid_create_graded). */

@@ -6,23 +6,16 @@ zero state on a grid with per-cell permittivity ``eps_r`` (a float32 CUDA
 tensor of shape (nz, ny, nx)); ``J.backward()`` gives dJ/d eps_r from the
 adjoint sweep of libfitgb (fit_adjoint_grad).  ``spacing`` holds three
 steps, or per-cell sizes along an axis for a graded grid; L_p is then the
-size of the cell the probe edge runs through along its axis.  Torch only holds the tensors
-and the stream: the run and its gradient are the library's kernels.
+size of the cell the probe edge runs through along its axis.  Torch only
+holds the tensors and the stream: the run, J and its gradient all come from
+the library (without a gradient request, fit_adjoint_grad runs the forward
+pass and J only).
 """
 from __future__ import annotations
 
-import numpy as np
 import torch
 
 from . import fitgb
-
-
-def edge_length(spacing, p):
-    """Length of probe p's edge: the step along its axis, or on a graded axis
-    the size of the cell at the probe's index along it."""
-    a = p["axis"]
-    d = spacing[a]
-    return float(d) if np.ndim(d) == 0 else float(np.asarray(d)[(p["i"], p["j"], p["k"])[a]])
 
 
 class ProbeEnergy(torch.autograd.Function):
@@ -36,15 +29,11 @@ class ProbeEnergy(torch.autograd.Function):
         stream = torch.cuda.current_stream(dev)
         try:
             J = torch.zeros(1, dtype=torch.float64, device=dev)
-            if ctx.needs_input_grad[0]:
-                grad = torch.zeros((nz, ny, nx), dtype=torch.float64, device=dev)
-                fitgb.fit_adjoint_grad(g.handle, dt, nsteps, sources, probes, ckpt_every, J, grad, stream=stream)
+            # without a gradient request the library runs the forward pass only
+            grad = torch.zeros((nz, ny, nx), dtype=torch.float64, device=dev) if ctx.needs_input_grad[0] else None
+            fitgb.fit_adjoint_grad(g.handle, dt, nsteps, sources, probes, ckpt_every, J, grad, stream=stream)
+            if grad is not None:
                 ctx.save_for_backward(grad)
-            else:
-                pr = torch.zeros((nsteps, len(probes)), dtype=torch.float64, device=dev)
-                fitgb.fit_leapfrog_run(g.handle, dt, nsteps, 0, sources, probes, pr, stream=stream)
-                L = torch.tensor([edge_length(spacing, p) for p in probes], dtype=torch.float64, device=dev)
-                J = ((pr / L) ** 2).sum().reshape(1)
             torch.cuda.synchronize(dev)
         finally:
             g.close()

@@ -21,23 +21,27 @@ int adjoint_impl(fit_grid *g, double dt, long long N, const fit_source *src, int
     g->stats = fit_run_stats{0, 0, 0, 0.0, 0.0, 0, 0, 0.0, 0.0};
     if (nprb < 1 || nprb > kMaxSrc || nsrc > kMaxSrc) return FIT_ERR_UNSUPPORTED;
     if ((rc = ensure_coeffs<T>(g, dt, scheme, false, s))) return rc;
+    // without a gradient output only the forward run and J are computed: no
+    // checkpoints and no reverse sweep
+    const bool want_grad = grad_out != nullptr;
     if (C <= 0) C = std::max(1, (int)std::ceil(std::sqrt((double)N)));
     if (C > N) C = (int)N;
+    if (!want_grad) C = 1;
     const long long nseg = (N + C - 1) / C;
     const long long ncp = g->ncp;
     const size_t n6 = 6 * (size_t)ncp;
-    if ((rc = ensure(g->ckpt, (size_t)nseg * n6 * sizeof(T)))) return rc;
+    if (want_grad && (rc = ensure(g->ckpt, (size_t)nseg * n6 * sizeof(T)))) return rc;
     if ((rc = ensure(g->ring, (size_t)(C + 1) * n6 * sizeof(T)))) return rc;
-    if ((rc = ensure(g->lam, 2 * n6 * sizeof(T)))) return rc;
-    if ((rc = ensure(g->gacc, 3 * (size_t)ncp * sizeof(double)))) return rc;
+    if (want_grad && (rc = ensure(g->lam, 2 * n6 * sizeof(T)))) return rc;
+    if (want_grad && (rc = ensure(g->gacc, 3 * (size_t)ncp * sizeof(double)))) return rc;
     // FP32 fields: the gradient of each block of kGradBlock adjoint steps is summed in FP32 and
     // then added into the FP64 total (block boundaries fixed in the adjoint step index, so the
     // result does not depend on the checkpoint interval)
     constexpr int kGradBlock = 64;
-    const bool fp32_blocks = sizeof(T) == 4;
+    const bool fp32_blocks = want_grad && sizeof(T) == 4;
     if (fp32_blocks && (rc = ensure(g->gblk, 3 * (size_t)ncp * sizeof(float)))) return rc;
     if ((rc = ensure(g->aprobe, (size_t)N * nprb * sizeof(double)))) return rc;
-    if ((rc = ensure(g->aamp, (size_t)N * nprb * sizeof(double)))) return rc;
+    if (want_grad && (rc = ensure(g->aamp, (size_t)N * nprb * sizeof(double)))) return rc;
     if ((rc = ensure(g->adjmem, (size_t)(C + 2) * sizeof(Member)))) return rc;
     if ((rc = ensure(g->err, sizeof(int)))) return rc;
     if ((rc = ensure(g->scalar, 2 * sizeof(double)))) return rc;
@@ -51,8 +55,10 @@ int adjoint_impl(fit_grid *g, double dt, long long N, const fit_source *src, int
     T *ring = (T *)g->ring.p, *lam = (T *)g->lam.p, *ckpt = (T *)g->ckpt.p;
     double *gacc = (double *)g->gacc.p, *aprobe = (double *)g->aprobe.p, *aamp = (double *)g->aamp.p;
     FIT_CHECK(cudaMemsetAsync(ring, 0, n6 * sizeof(T), s));
-    FIT_CHECK(cudaMemsetAsync(lam, 0, 2 * n6 * sizeof(T), s));
-    FIT_CHECK(cudaMemsetAsync(gacc, 0, 3 * (size_t)ncp * sizeof(double), s));
+    if (want_grad) {
+        FIT_CHECK(cudaMemsetAsync(lam, 0, 2 * n6 * sizeof(T), s));
+        FIT_CHECK(cudaMemsetAsync(gacc, 0, 3 * (size_t)ncp * sizeof(double), s));
+    }
     if (fp32_blocks) FIT_CHECK(cudaMemsetAsync(g->gblk.p, 0, 3 * (size_t)ncp * sizeof(float), s));
     FIT_CHECK(cudaMemsetAsync(g->err.p, 0, sizeof(int), s));
 
@@ -90,8 +96,8 @@ int adjoint_impl(fit_grid *g, double dt, long long N, const fit_source *src, int
     if (tile.kernel == 2 &&
         !(encode_tma_maps(&ring_maps, (int)sizeof(T), g->nx, g->ny, g->nz, g->pitch, ring, C + 1, g->coef.p,
                           g->lossy ? 6 : 3, tile.tx, tile.ty) &&
-          encode_tma_maps(&lam_maps, (int)sizeof(T), g->nx, g->ny, g->nz, g->pitch, lam, 2, g->coef.p,
-                          g->lossy ? 6 : 3, tile.tx, tile.ty))) {
+          (!want_grad || encode_tma_maps(&lam_maps, (int)sizeof(T), g->nx, g->ny, g->nz, g->pitch, lam, 2,
+                                         g->coef.p, g->lossy ? 6 : 3, tile.tx, tile.ty)))) {
         tile.kernel = 1;
         if (!tile_supported(tile.tx, tile.ty)) tile.tx = 32, tile.ty = 8;
     }
@@ -128,7 +134,7 @@ int adjoint_impl(fit_grid *g, double dt, long long N, const fit_source *src, int
     for (int q = 0; q < nprb; ++q) a.prb[q] = {prb[q].axis, prb[q].i, prb[q].j, prb[q].k};
     a.mem = mdev;
     for (long long n = 0; n < N; ++n) {
-        if (n % C == 0)
+        if (want_grad && n % C == 0)
             FIT_CHECK(cudaMemcpyAsync(ckpt + (size_t)(n / C) * n6, ring + (size_t)(n & 1) * n6, n6 * sizeof(T),
                                       cudaMemcpyDeviceToDevice, s));
         a.it = (int)n;
@@ -146,11 +152,16 @@ int adjoint_impl(fit_grid *g, double dt, long long N, const fit_source *src, int
     }
     double *Jdev = (double *)g->scalar.p;
     FIT_CHECK(probe_functional(prb, nprb, plen, aprobe, N, Jdev, s));
+    g->stats.kernel_launches += 1;
+    if (!want_grad) {
+        if (J_out) FIT_CHECK(cudaMemcpyAsync(J_out, Jdev, sizeof(double), kind_from_dev(J_out), s));
+        return finish(g, s, J_out && !is_device(J_out));
+    }
     // adjoint state at N and the adjoint sources
     FIT_CHECK(adjoint_init<T>(prb, nprb, plen, aprobe + (size_t)(N - 1) * nprb, (const T *)g->coef.p, lam, g->pitch,
                               g->ny, ncp, s));
     FIT_CHECK(adjoint_sources(prb, nprb, plen, aprobe, N, aamp, s));
-    g->stats.kernel_launches += 3;
+    g->stats.kernel_launches += 2;
     // -eps0 A_a / (L_a dt) per axis; on a graded grid the geometry goes into the scatter
     const double K[3] = {g->graded ? -kEps0 / dt : -kEps0 * (g->d[1] * g->d[2] / g->d[0]) / dt,
                          g->graded ? -kEps0 / dt : -kEps0 * (g->d[2] * g->d[0] / g->d[1]) / dt,
@@ -196,8 +207,8 @@ int adjoint_impl(fit_grid *g, double dt, long long N, const fit_source *src, int
     }
     // per-cell gradient and J
     double *gout = grad_out;
-    const bool grad_host = grad_out && !is_device(grad_out);
-    if (grad_host || !grad_out) {
+    const bool grad_host = !is_device(grad_out);
+    if (grad_host) {
         if ((rc = ensure(g->grad_ws, sizeof(double) * (size_t)g->ncell))) return rc;
         gout = (double *)g->grad_ws.p;
     }
@@ -226,7 +237,7 @@ int fit_adjoint_grad(fit_grid *g, double dt, long nsteps, const fit_source *src,
     cudaStream_t s = (cudaStream_t)stream;
     if (g->prec == 64)
         return adjoint_impl<double>(g, dt, nsteps, src, nsrc, prb, nprb, ckpt_every, J_out, grad_eps_r, opts, s);
-    if (g->prec == 48) return FIT_ERR_UNSUPPORTED;
+    if (g->prec == 48 || g->prec == 40) return FIT_ERR_UNSUPPORTED;
     return adjoint_impl<float>(g, dt, nsteps, src, nsrc, prb, nprb, ckpt_every, J_out, grad_eps_r, opts, s);
 }
 

@@ -32,7 +32,8 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
     const long long ncell = g->ncell;   // real cells (algorithmic counts)
     const long long ncp = g->ncp;       // padded component stride (device arrays)
     const bool comp = g->prec == 48;    // hi/lo float pairs: 12-component state blocks
-    const size_t n6 = (comp ? 12 : 6) * (size_t)ncp;
+    const bool resf = g->prec == 40;    // floats + bfloat16 residual words: 9-component state blocks
+    const size_t n6 = (comp ? 12 : (resf ? 9 : 6)) * (size_t)ncp;
     const size_t row = (size_t)g->nx * sizeof(T), prow = (size_t)g->pitch * sizeof(T);
     const size_t rows3 = 3 * (size_t)g->ny * g->nz;
     int rc;
@@ -43,7 +44,7 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
     long long nev = 0;   // events recorded (pairs around step launches)
     // algorithmic bytes of one step launch: fields of every member once in and
     // once out, plus the coefficient arrays once
-    const double fld_bytes = (comp ? 24.0 : 12.0) * sizeof(T) * (double)ncell;
+    const double fld_bytes = (comp ? 24.0 : (resf ? 18.0 : 12.0)) * sizeof(T) * (double)ncell;
     const double coef_bytes = ((g->lossy ? 6.0 : 3.0) + (g->mu_array ? 3.0 : 0.0) +
                                (energy_dev ? (3.0 + (g->mu_array ? 3.0 : 0.0)) : 0.0)) * sizeof(T) * (double)ncell;
 
@@ -71,7 +72,7 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
     FIT_CHECK(cudaMemsetAsync(g->err.p, 0, sizeof(int), s));
     if (probes) FIT_CHECK(cudaMemsetAsync(g->pm.p, 0, sizeof(double) * (size_t)probe_rows * nprb * nm_total, s));
     if (energy_dev) FIT_CHECK(cudaMemsetAsync(energy_dev, 0, sizeof(double) * (size_t)specs_in[0].nit, s));
-    const bool kahan = sum_mode == 1 && acc_e && !comp;
+    const bool kahan = sum_mode == 1 && acc_e && !comp && !resf;
     if (kahan) {
         if ((rc = ensure(g->kahan, 2 * n6 * sizeof(float)))) return rc;
         FIT_CHECK(cudaMemsetAsync(g->kahan.p, 0, 2 * n6 * sizeof(float), s));
@@ -104,7 +105,12 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
     a.wait_limit = opts ? std::max(0, opts->debug_wait_limit) : 0;
     a.extra_tx = opts ? std::max(0, opts->debug_extra_tx) : 0;
     TmaMaps maps;
-    if (comp) {
+    if (resf) {
+        if (!res_tile_supported(tile.tx, tile.ty)) tile.tx = 64, tile.ty = 4;
+        if (!encode_tma_maps(&maps, (int)sizeof(T), g->nx, g->ny, g->nz, g->pitch, g->state.p, 2 * mpp, g->coef.p,
+                             g->lossy ? 6 : 3, tile.tx, tile.ty, 9))
+            return FIT_ERR_UNSUPPORTED;
+    } else if (comp) {
         if (!comp_tile_supported(tile.tx, tile.ty)) tile.tx = 32, tile.ty = 8;
         if (!encode_tma_maps(&maps, (int)sizeof(T), g->nx, g->ny, g->nz, g->pitch, g->state.p, 2 * mpp, g->coef.p,
                              g->lossy ? 6 : 3, tile.tx, tile.ty, 12))
@@ -122,7 +128,7 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
         for (int part = 0; part < 2; ++part) {
             void *dst = part ? final_h : final_e;
             if (!dst) continue;
-            if (!comp) {
+            if (!comp && !resf) {
                 FIT_CHECK(cudaMemcpy2DAsync(dst, row, fin + 3 * part * ncp, prow, row, rows3, kind_from_dev(dst), s));
                 continue;
             }
@@ -133,8 +139,11 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
                 if ((r2 = ensure(g->stage, 3 * (size_t)ncell * sizeof(double)))) return r2;
                 dout = (double *)g->stage.p;
             }
-            FIT_CHECK(join_pairs(g->nx, g->ny, g->nz, g->pitch, (const float *)(fin + 3 * part * ncp),
-                                 (const float *)(fin + (6 + 3 * part) * ncp), dout, s));
+            if (resf)
+                FIT_CHECK(join_res(g->nx, g->ny, g->nz, g->pitch, (const float *)fin, part, dout, s));
+            else
+                FIT_CHECK(join_pairs(g->nx, g->ny, g->nz, g->pitch, (const float *)(fin + 3 * part * ncp),
+                                     (const float *)(fin + (6 + 3 * part) * ncp), dout, s));
             if (host)
                 FIT_CHECK(cudaMemcpyAsync(dst, dout, 3 * (size_t)ncell * sizeof(double), cudaMemcpyDeviceToHost, s));
         }
@@ -146,7 +155,8 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
     TmaMaps maps2;
     CUtensorMap coefwin;
     Tile tile2 = {32, 8, tile.kz, 2, 3};
-    if (opts && opts->steps_per_launch == 2 && sizeof(T) == 4 && !comp && !energy_dev && tile.kernel == 2) {
+    if (opts && opts->steps_per_launch == 2 && sizeof(T) == 4 && !comp && !resf && !energy_dev &&
+        tile.kernel == 2) {
         if (opts->tile_x > 0 && opts->tile_y > 0 && step2_tile_supported(opts->tile_x, opts->tile_y))
             tile2.tx = opts->tile_x, tile2.ty = opts->tile_y;
         two = encode_tma_maps(&maps2, 4, g->nx, g->ny, g->nz, g->pitch, g->state.p, 2 * mpp, g->coef.p,
@@ -188,7 +198,19 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
             mem[q].energy_base = sp.start;
             // initial state into buffer 0
             FIT_CHECK(cudaMemsetAsync(base, 0, n6 * sizeof(T), s));
-            if (comp) {   // FP64 compact input -> hi/lo pairs (masked to the degrees of freedom)
+            if (resf && (sp.e0 || sp.h0)) {   // FP64 compact input -> floats + residual words (masked)
+                const double *din[2] = {(const double *)sp.e0, (const double *)sp.h0};
+                const size_t n3d = 3 * (size_t)ncell * sizeof(double);
+                for (int part = 0; part < 2; ++part) {
+                    if (!din[part] || is_device(din[part])) continue;
+                    if ((rc = ensure(g->stage, 2 * n3d))) return rc;
+                    double *dst = (double *)g->stage.p + part * 3 * (size_t)ncell;
+                    FIT_CHECK(cudaMemcpyAsync(dst, din[part], n3d, cudaMemcpyHostToDevice, s));
+                    din[part] = dst;
+                }
+                FIT_CHECK(split_res(g->nx, g->ny, g->nz, g->pitch, din[0], din[1], (float *)base, s));
+                g->stats.kernel_launches += 1;
+            } else if (comp) {   // FP64 compact input -> hi/lo pairs (masked to the degrees of freedom)
                 for (int part = 0; part < 2; ++part) {
                     const void *src0 = part ? sp.h0 : sp.e0;
                     if (!src0) continue;
@@ -209,7 +231,7 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
                 if (sp.h0)
                     FIT_CHECK(cudaMemcpy2DAsync(base + 3 * ncp, prow, sp.h0, row, row, rows3, kind_to_dev(sp.h0), s));
             }
-            if (!comp && (sp.e0 || sp.h0)) {
+            if (!comp && !resf && (sp.e0 || sp.h0)) {
                 FIT_CHECK(mask_state<T>(g->nx, g->ny, g->nz, g->pitch, base, base + 3 * ncp, s));
                 g->stats.kernel_launches += 1;
             }
@@ -293,7 +315,10 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
                 }
                 FIT_CHECK(cudaEventRecord(g->ev[2 * nev], s));
             }
-            if (comp)
+            if (resf)
+                FIT_CHECK(launch_step_res((const StepArgs<float> &)a, maps, tile, g->lossy, g->mu_array,
+                                          energy_dev != nullptr, s));
+            else if (comp)
                 FIT_CHECK(launch_step_comp((const StepArgs<float> &)a, maps, tile, g->lossy, g->mu_array,
                                            energy_dev != nullptr, s));
             else if (tile.kernel == 2)
@@ -318,6 +343,13 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
                         float *ks = (float *)g->kahan.p;
                         FIT_CHECK(accumulate_state_kahan<T>((long long)n6, fin, ks, ks + n6, s));
                         g->stats.kernel_launches += 1;
+                    } else if (resf) {
+                        FIT_CHECK(accumulate_res(ncp, (const float *)fin, 0, acc_e, s));
+                        g->stats.kernel_launches += 1;
+                        if (acc_h) {
+                            FIT_CHECK(accumulate_res(ncp, (const float *)fin, 1, acc_h, s));
+                            g->stats.kernel_launches += 1;
+                        }
                     } else if (comp) {
                         FIT_CHECK(accumulate_pairs(3 * ncp, (const float *)fin, (const float *)(fin + 6 * ncp),
                                                    acc_e, s));
@@ -347,7 +379,10 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
             const MemberSpec &sp = specs_in[order[first + q]];
             if (sp.nit > 0) continue;
             const T *fin = (const T *)mem[q].st[0];
-            if (acc_e && comp) {
+            if (acc_e && resf) {
+                FIT_CHECK(accumulate_res(ncp, (const float *)fin, 0, acc_e, s));
+                if (acc_h) FIT_CHECK(accumulate_res(ncp, (const float *)fin, 1, acc_h, s));
+            } else if (acc_e && comp) {
                 FIT_CHECK(accumulate_pairs(3 * ncp, (const float *)fin, (const float *)(fin + 6 * ncp), acc_e, s));
                 if (acc_h)
                     FIT_CHECK(accumulate_pairs(3 * ncp, (const float *)(fin + 3 * ncp), (const float *)(fin + 9 * ncp),
@@ -502,7 +537,7 @@ int fit_grid_create(int nx, int ny, int nz, double dx, double dy, double dz, con
     if (flags & ~FIT_FLAG_COEF_FLOAT) return FIT_ERR_ARG;
     if (!(dx > 0) || !(dy > 0) || !(dz > 0) || !std::isfinite(dx) || !std::isfinite(dy) || !std::isfinite(dz))
         return FIT_ERR_ARG;
-    if (precision != 32 && precision != 64 && precision != 48) return FIT_ERR_ARG;
+    if (precision != 32 && precision != 64 && precision != 48 && precision != 40) return FIT_ERR_ARG;
     const long long ncell = (long long)nx * ny * nz;
     if (ncell > (1LL << 34)) return FIT_ERR_ARG;
     fit_grid *g = new (std::nothrow) fit_grid();
@@ -622,7 +657,7 @@ int fit_leapfrog_run(fit_grid *g, double dt, long nsteps, long step0, const fit_
     if (g->prec == 64)
         return leapfrog_impl<double>(g, dt, nsteps, step0, src, nsrc, prb, nprb, probe_out, energy_out, e_io, h_io,
                                      opts, s);
-    if (g->prec == 48 && opts && opts->kernel == 1) return FIT_ERR_UNSUPPORTED;
+    if ((g->prec == 48 || g->prec == 40) && opts && opts->kernel == 1) return FIT_ERR_UNSUPPORTED;
     return leapfrog_impl<float>(g, dt, nsteps, step0, src, nsrc, prb, nprb, probe_out, energy_out, e_io, h_io, opts,
                                 s);
 }
@@ -642,7 +677,7 @@ int paraexp_run(fit_grid *g, double dt, int K, const long *win, const fit_source
     if (opts && opts->homogeneous != FIT_HOMOG_LEAPFROG) {
         if (opts->homogeneous != FIT_HOMOG_LEJA && opts->homogeneous != FIT_HOMOG_TAYLOR) return FIT_ERR_ARG;
         if (opts->sum_mode != 0) return FIT_ERR_ARG;
-        if (g->prec == 48 || g->lossy) return FIT_ERR_UNSUPPORTED;
+        if (g->prec == 48 || g->prec == 40 || g->lossy) return FIT_ERR_UNSUPPORTED;
         if (g->prec == 64)
             return paraexp_expo_impl<double>(g, dt, K, win, src, nsrc, prb, nprb, probe_out, e_final, h_final, e0,
                                              h0, opts, s);
@@ -651,7 +686,8 @@ int paraexp_run(fit_grid *g, double dt, int K, const long *win, const fit_source
     }
     if (g->prec == 64)
         return paraexp_impl<double>(g, dt, K, win, src, nsrc, prb, nprb, probe_out, e_final, h_final, e0, h0, opts, s);
-    if (g->prec == 48 && opts && (opts->kernel == 1 || opts->sum_mode == 1)) return FIT_ERR_UNSUPPORTED;
+    if ((g->prec == 48 || g->prec == 40) && opts && (opts->kernel == 1 || opts->sum_mode == 1))
+        return FIT_ERR_UNSUPPORTED;
     return paraexp_impl<float>(g, dt, K, win, src, nsrc, prb, nprb, probe_out, e_final, h_final, e0, h0, opts, s);
 }
 

@@ -462,7 +462,7 @@ int fit_expo_propagate(fit_grid *g, double dt, long nsteps, const fit_probe *prb
     if (opts->homogeneous != FIT_HOMOG_LEJA && opts->homogeneous != FIT_HOMOG_TAYLOR) return FIT_ERR_ARG;
     int rc;
     if ((rc = check_sources_probes(g, nullptr, 0, prb, nprb))) return rc;
-    if (g->prec == 48 || g->lossy) return FIT_ERR_UNSUPPORTED;
+    if (g->prec == 48 || g->prec == 40 || g->lossy) return FIT_ERR_UNSUPPORTED;
     if (nsteps == 0) return FIT_OK;
     cudaStream_t s = (cudaStream_t)stream;
     if (g->prec == 64)

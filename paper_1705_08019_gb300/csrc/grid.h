@@ -166,7 +166,7 @@ struct MemberSpec {
 inline Tile pick_tile(const fit_grid *g, const fit_run_opts *o) {
     Tile t = g->tile;
     // FP32 default: 64 x 4 tiles, a 3-plane ring (4 CTAs per SM), 64-plane chunks
-    if (g->prec == 32 && !g->tile_fixed) t = Tile{64, 4, 64, 2, 3};
+    if ((g->prec == 32 || g->prec == 40) && !g->tile_fixed) t = Tile{64, 4, 64, 2, 3};
     if (o && o->kernel > 0) t.kernel = o->kernel;
     if (o && o->tile_x > 0 && o->tile_y > 0) {
         t.tx = o->tile_x;
@@ -176,6 +176,9 @@ inline Tile pick_tile(const fit_grid *g, const fit_run_opts *o) {
     if (g->prec == 48) {
         if (!comp_tile_supported(t.tx, t.ty)) t.tx = 32, t.ty = 8;
         t.kernel = 2;
+    } else if (g->prec == 40) {
+        if (!res_tile_supported(t.tx, t.ty)) t.tx = 64, t.ty = 4;
+        t.kernel = (o && o->kernel == 3) ? 3 : 2;
     } else if (t.kernel == 2 && !tma_tile_supported(t.tx, t.ty, g->prec == 64 ? 8 : 4)) {
         t.kernel = 1;
     }

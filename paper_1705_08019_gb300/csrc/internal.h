@@ -158,6 +158,19 @@ cudaError_t launch_step_comp(const StepArgs<float> &a, const TmaMaps &maps, Tile
                              bool energy, cudaStream_t s);
 bool comp_tile_supported(int tx, int ty);
 
+// step_res.cu: FP32 fields with bfloat16 residuals (9-component state blocks: 6 hi floats, then the residual
+// words (lo e_x, lo e_y), (lo e_z, lo h_x), (lo h_y, lo h_z))
+cudaError_t launch_step_res(const StepArgs<float> &a, const TmaMaps &maps, Tile tile, bool lossy, bool mu_array,
+                            bool energy, cudaStream_t s);
+bool res_tile_supported(int tx, int ty);
+// FP64 compact e, h (either may be null = zero) -> one padded state block, masked to the degrees of freedom
+cudaError_t split_res(int nx, int ny, int nz, int pitch, const double *e, const double *h, float *state,
+                      cudaStream_t s);
+// part 0 (e) or 1 (h) of a state block -> FP64 compact fields
+cudaError_t join_res(int nx, int ny, int nz, int pitch, const float *state, int part, double *out, cudaStream_t s);
+// acc[t] += part 0 (e) or 1 (h) of a state block, padded layout (3*ncp values)
+cudaError_t accumulate_res(long long ncp, const float *state, int part, double *acc, cudaStream_t s);
+
 // aux.cu
 struct MaterialFlags {
     int bad_eps, bad_mu, bad_sigma, mu_nonuniform, lossy;

@@ -390,8 +390,8 @@ class Grid:
     def __init__(self, dims, spacing, eps_r, mu_r=None, sigma=None, precision=32, flags=0):
         self.dims = tuple(int(v) for v in dims)
         self.precision = int(precision)
-        # precision 48: compensated FP32 fields (hi + lo float pairs), FP64 I/O
-        self.dtype = np.float64 if precision in (64, 48) else np.float32
+        # precision 40 (FP32 + bfloat16 residual) and 48 (float pairs): FP64 I/O
+        self.dtype = np.float64 if precision in (64, 48, 40) else np.float32
         if all(np.ndim(v) == 0 for v in spacing):
             self.spacing = tuple(float(v) for v in spacing)
             self.handle = fit_grid_create(dims, spacing, eps_r, mu_r, sigma, precision, flags)

@@ -48,17 +48,3 @@ def test_product_path_does_not_import_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "fit_oracle" not in text, f
-
-
-def test_autograd_probe_edge_lengths():
-    """The autograd binding's functional divides each probe by its edge's
-    length: the axis step, or on a graded axis the size of the cell at the
-    probe's index (as fit_adjoint_grad does)."""
-    import numpy as np
-    from paper_1705_08019_gb300.autograd import edge_length
-    uniform = (1e-3, 2e-3, 3e-3)
-    assert [edge_length(uniform, dict(axis=a, i=1, j=2, k=3)) for a in range(3)] == [1e-3, 2e-3, 3e-3]
-    graded = (np.array([1.0, 2.0, 3.0]), 5.0, np.array([7.0, 8.0]))
-    assert edge_length(graded, dict(axis=0, i=2, j=0, k=1)) == 3.0
-    assert edge_length(graded, dict(axis=1, i=2, j=0, k=1)) == 5.0
-    assert edge_length(graded, dict(axis=2, i=2, j=0, k=1)) == 8.0
