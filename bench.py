@@ -52,9 +52,12 @@ def parse():
     ap.add_argument("--kernel", type=int, default=0, help="opts.kernel of the solve [0 = the library's default]")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the field error, plain FP32, sequential, batched and adjoint sections")
     ap.add_argument("--compare-plain", action="store_true",
                     help="also time the K windows run one after another (members_per_pass=1)")
-    ap.add_argument("--ncu-case", choices=["leapfrog", "paraexp", "expo", "batch"], default=None,
+    ap.add_argument("--side", type=int, default=None, help="boxes workload: cells per side [256]")
+    ap.add_argument("--ncu-case", choices=["leapfrog", "paraexp", "solve", "expo", "batch"], default=None,
                     help="run a short untimed case for an ncu capture and exit (no JSON line)")
     ap.add_argument("--ncu-steps", type=int, default=8)
     ap.add_argument("--ncu-members", type=int, default=4)
@@ -83,9 +86,15 @@ def load_workload(name, args=None):
     if name == "batch64":
         return W.cavity_batch()
     if name == "boxes256":
-        w = W.boxes256(nsteps=args.nsteps) if args is not None and args.nsteps else W.boxes256()
-        if args is not None and args.precision:
-            w.precision = args.precision
+        kw = {}
+        if args is not None and args.nsteps:
+            kw["nsteps"] = args.nsteps
+        if args is not None and args.side:
+            kw["n_side"] = args.side
+        w = W.boxes256(**kw)
+        # the headline path: FP32 fields with a bfloat16 residual, the field representation that
+        # meets the 1e-5 field-error target (plain FP32 is measured beside it)
+        w.precision = args.precision if args is not None and args.precision else 40
         return w
     if name == "cavity16":
         return W.cavity16()
@@ -129,7 +138,7 @@ def oracle_sample(w, nsteps=4, K=2):
     oracle.build()
     t0 = time.perf_counter()
     dt = w.cfl_fraction * oracle.cfl_dt(w.dims, w.spacing, w.eps_r, w.mu_r)
-    g = oracle.OracleGrid(w.dims, w.spacing, w.eps_r, w.mu_r, w.sigma, dt=dt, round32=(w.precision == 32))
+    g = oracle.OracleGrid(w.dims, w.spacing, w.eps_r, w.mu_r, w.sigma, dt=dt, round32=(w.precision != 64))
     win = np.array([(j * nsteps) // K for j in range(K + 1)], dtype=np.int64)
     g.paraexp(K, win, w.sources, w.probes)
     sec = time.perf_counter() - t0
@@ -212,11 +221,19 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def traffic_from_profile():
+# ncu summary of each precision's step kernel: (profile, kernel source, hash key)
+PROFILES = {32: ("step_tma_kernel_boxes256.md", "step_tma.cuh", "step_tma_cuh_sha256"),
+            40: ("step_res2_kernel_boxes256.md", "step_res.cu", "step_res_cu_sha256")}
+
+
+def traffic_from_profile(precision=32):
     """Measured DRAM bytes / algorithmic bytes of the step kernel from the
     committed ncu summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "step_tma_kernel_boxes256.md")
-    src = os.path.join(ROOT, "paper_1705_08019_gb300", "csrc", "step_tma.cuh")
+    if precision not in PROFILES:
+        return None
+    prof, src_name, key = PROFILES[precision]
+    path = os.path.join(ROOT, "profiles", prof)
+    src = os.path.join(ROOT, "paper_1705_08019_gb300", "csrc", src_name)
     if not os.path.exists(path):
         return None
     vals = {}
@@ -225,7 +242,7 @@ def traffic_from_profile():
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if vals.get("step_tma_cuh_sha256") != sha:
+    if vals.get(key) != sha:
         return None
     try:
         return float(vals["dram_over_algorithmic"])
@@ -255,6 +272,52 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def rel_l2(x, ref):
+    """max over components (or probe columns) of ||x - ref||_2 / ||ref||_2."""
+    import torch
+    x = x.double().reshape(x.shape[0], -1)
+    ref = ref.double().reshape(ref.shape[0], -1)
+    num = torch.linalg.vector_norm(x - ref, dim=1)
+    den = torch.linalg.vector_norm(ref, dim=1).clamp_min(1e-300)
+    return float((num / den).max())
+
+
+def field_errors(pr, ef, hf, ref):
+    """Relative L2 errors of probe traces and final e, h against (pr, e, h) of a reference run."""
+    out = {"probes": rel_l2(pr.T, ref[0].T), "e": rel_l2(ef, ref[1]), "h": rel_l2(hf, ref[2])}
+    out["max"] = max(out.values())
+    return out
+
+
+def fp64_reference(fitgb, w, eps_d, mu_d, sig_d, dt, stream):
+    """One sequential FP64 leapfrog run of the workload on the float-rounded
+    coefficients (FIT_FLAG_COEF_FLOAT): probe trace and final e, h.  In exact
+    arithmetic ParaExp's superposition equals this run."""
+    import torch
+    nx, ny, nz = w.dims
+    dev = eps_d.device
+    g = fitgb.fit_grid_create(w.dims, w.spacing, eps_d, mu_d, sig_d, 64, fitgb.FIT_FLAG_COEF_FLOAT)
+    pr = torch.zeros((w.nsteps, len(w.probes)), dtype=torch.float64, device=dev)
+    e = torch.zeros((3, nz, ny, nx), dtype=torch.float64, device=dev)
+    h = torch.zeros_like(e)
+    fitgb.fit_leapfrog_run(g, dt, w.nsteps, 0, w.sources, w.probes, pr, None, e, h, stream=stream)
+    torch.cuda.synchronize()
+    fitgb.fit_grid_destroy(g)
+    return pr, e, h
+
+
+def timed(stream, fn):
+    """Device milliseconds of fn() by CUDA events on `stream` (synchronized on both sides)."""
+    import torch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), r
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_1705_08019_gb300 import build as B
@@ -281,8 +344,8 @@ def run_ours(args, rank, world, local_rank):
     dt = w.cfl_fraction * fitgb.fit_cfl_dt(g0)
     fitgb.fit_grid_destroy(g0)
 
-    def step(profile=True, members_per_pass=0):
-        g = fitgb.fit_grid_create(w.dims, w.spacing, eps_d, mu_d, sig_d, w.precision)
+    def step(profile=True, members_per_pass=0, precision=None):
+        g = fitgb.fit_grid_create(w.dims, w.spacing, eps_d, mu_d, sig_d, precision or w.precision)
         fitgb.paraexp_run(g, dt, w.K, win, w.sources, w.probes, probe_d, ef_d, hf_d,
                           opts=fitgb.make_opts(profile=int(profile), members_per_pass=members_per_pass,
                                                kernel=args.kernel),
@@ -316,31 +379,68 @@ def run_ours(args, rank, world, local_rank):
     cells_per_step = stats[0]["cell_updates"]
     assert cells_per_step == work_of(w), (cells_per_step, work_of(w))
     value = world * cells_per_step / (ms / 1e3) / 1e9
-    step_ms = sum(s["step_ms"] for s in stats)
-    alg = sum(s["alg_bytes"] for s in stats)
-    launches = sum(s["step_launches"] for s in stats)
     peak, peak_kind = peaks()
-    achieved = alg / (step_ms / 1e3) / 1e9 if step_ms > 0 else None
-    ratio = traffic_from_profile()
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": (achieved / peak) if achieved else None,
-            "traffic": (ratio * alg / launches) if ratio else None,
-            "peak_kind": f"{peak_kind} copy bandwidth",
-            "kernel": "step_tma_kernel (fused E/H leapfrog, TMA ring, all active members)",
-            "alg_bytes_per_launch": alg / launches, "avg_launch_us": 1e3 * step_ms / launches,
-            "step_kernel_share": step_ms / (ms * args.steps)}
+
+    def roofline(sts, total_ms, kernel_name, ratio=None):
+        step_ms = sum(s["step_ms"] for s in sts)
+        alg = sum(s["alg_bytes"] for s in sts)
+        launches = sum(s["step_launches"] for s in sts)
+        achieved = alg / (step_ms / 1e3) / 1e9 if step_ms > 0 else None
+        return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": (ratio * alg / launches) if ratio else None,
+                "peak_kind": f"{peak_kind} copy bandwidth", "kernel": kernel_name,
+                "alg_bytes_per_launch": alg / launches, "avg_launch_us": 1e3 * step_ms / launches,
+                "step_kernel_share": step_ms / total_ms}
+
+    kernel_name = {32: "step_tma_kernel (FP32 fields)", 40: "step_res2_kernel (FP32 + bfloat16 residual, two "
+                   "cells per thread)", 48: "step_comp_kernel (float pairs)", 64: "step_tma_kernel (FP64)"}
+    roof = roofline(stats, ms * args.steps,
+                    kernel_name[w.precision] + ": fused E/H leapfrog, TMA ring, all active members",
+                    traffic_from_profile(w.precision))
     extras = {}
-    if args.compare_plain and rank == 0:
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step(profile=False, members_per_pass=1)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        plain_ms = e0.elapsed_time(e1)
-        extras["plain_per_window_ms"] = plain_ms
-        extras["batched_speedup_vs_plain"] = plain_ms / ms
+    if rank == 0 and not args.no_extras and args.workload == "boxes256":
+        res_pr, res_e, res_h = probe_d.clone(), ef_d.clone(), hf_d.clone()
+        ref = fp64_reference(fitgb, w, eps_d, mu_d, sig_d, dt, stream)
+        extras["field_error"] = dict(field_errors(res_pr, res_e, res_h, ref), target=1e-5,
+                                     reference="one sequential FP64 leapfrog run of all steps on the same "
+                                               "float-rounded coefficients (FIT_FLAG_COEF_FLOAT)",
+                                     metric="relative L2 per probe trace and per field component, max")
+        del res_pr, res_e, res_h
+        if w.precision != 32:   # the plain FP32 fields on the same solve, for comparison
+            pms, pst = timed(stream, lambda: step(precision=32))
+            extras["fp32_plain"] = {
+                "value": cells_per_step / (pms / 1e3) / 1e9, "unit": UNIT,
+                "roofline_frac": roofline([pst], pms, kernel_name[32])["frac"],
+                "field_error": field_errors(probe_d, ef_d, hf_d, ref)}
+        del ref
+        torch.cuda.empty_cache()
+        # time to solution: the same problem by one sequential leapfrog run through fit_leapfrog_run
+        g = fitgb.fit_grid_create(w.dims, w.spacing, eps_d, mu_d, sig_d, w.precision)
+        T = torch.float32 if w.precision == 32 else torch.float64
+        e_s = torch.zeros((3, nz, ny, nx), dtype=T, device=dev)
+        h_s = torch.zeros_like(e_s)
+        pr_s = torch.zeros((w.nsteps, len(w.probes)), dtype=torch.float64, device=dev)
+        seq = lambda: fitgb.fit_leapfrog_run(g, dt, w.nsteps, 0, w.sources, w.probes, pr_s, None, e_s, h_s,
+                                             opts=fitgb.make_opts(kernel=args.kernel), stream=stream)
+        seq()
+        seq_ms, _ = timed(stream, seq)
+        fitgb.fit_grid_destroy(g)
+        del e_s, h_s, pr_s
+        extras["seq_leapfrog_s"] = seq_ms / 1e3
+        extras["paraexp_over_sequential"] = ms / seq_ms
+        extras["time_to_solution_note"] = (
+            "with leapfrog homogeneous problems ParaExp does K(K+1)/2 window-solves of work for the K of one "
+            "sequential run; Gcell-updates/s counts all of them")
+        if args.compare_plain:
+            plain_ms, _ = timed(stream, lambda: step(profile=False, members_per_pass=1))
+            extras["plain_per_window_ms"] = plain_ms
+            extras["batched_speedup_vs_plain"] = plain_ms / ms
+        torch.cuda.empty_cache()
+        extras["batched"] = batched_section(args, fitgb, dev, stream, peak)
+        torch.cuda.empty_cache()
+        extras["adjoint"] = adjoint_section(fitgb, dev, stream, peak)
+        torch.cuda.empty_cache()
 
     e2e = None
     if not args.no_e2e:
@@ -349,11 +449,13 @@ def run_ours(args, rank, world, local_rank):
         pr_h = np.zeros((nt, len(w.probes)))
         ef_h = np.zeros((3, nz, ny, nx))
         hf_h = np.zeros((3, nz, ny, nx))
+        step(profile=False)   # the device-resident result to compare with
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
         g = fitgb.fit_grid_create(w.dims, w.spacing, w.eps_r, w.mu_r, w.sigma, w.precision)
-        fitgb.paraexp_run(g, dt, w.K, win, w.sources, w.probes, pr_h, ef_h, hf_h)
+        fitgb.paraexp_run(g, dt, w.K, win, w.sources, w.probes, pr_h, ef_h, hf_h,
+                          opts=fitgb.make_opts(kernel=args.kernel))
         e2e_s = time.perf_counter() - t0
         fitgb.fit_grid_destroy(g)
         e2e_s = reduce_max(e2e_s, dev)
@@ -378,6 +480,88 @@ def run_ours(args, rank, world, local_rank):
                 "gpu_launches": int(sum(s["kernel_launches"] for s in stats)), "clocks": ck}
         line.update(extras)
         print(json.dumps(line), flush=True)
+
+
+def batched_section(args, fitgb, dev, stream, peak):
+    """The batching configuration: 64 PEC cavities of uneven size (sides 32..160),
+    K = 8 windows each, 5000 steps, FP32: one persistent, graph-captured,
+    autotuned launch per iteration for all grids and members, against the 64
+    problems run as plain per-window solves (members_per_pass = 1), both timed
+    with CUDA events on the stream."""
+    import torch
+    ws = load_workload("batch64")
+    eps_d = [torch.from_numpy(w.eps_r).to(dev) for w in ws]
+    outs = [torch.zeros((w.nsteps, len(w.probes)), dtype=torch.float64, device=dev) for w in ws]
+    dts = []
+    for w, e in zip(ws, eps_d):
+        g = fitgb.fit_grid_create(w.dims, w.spacing, e, None, None, 32)
+        dts.append(w.cfl_fraction * fitgb.fit_cfl_dt(g))
+        fitgb.fit_grid_destroy(g)
+    work = sum(work_of(w) for w in ws)
+
+    def solve(plain=False):
+        gs = [fitgb.fit_grid_create(w.dims, w.spacing, e, None, None, 32) for w, e in zip(ws, eps_d)]
+        probs = [dict(grid=g, dt=dt, K=w.K, win=w.windows(), sources=w.sources, probes=w.probes, probe_out=o)
+                 for g, dt, w, o in zip(gs, dts, ws, outs)]
+        if plain:
+            for q in probs:
+                fitgb.paraexp_run(q["grid"], q["dt"], q["K"], q["win"], q["sources"], q["probes"], q["probe_out"],
+                                  opts=fitgb.make_opts(members_per_pass=1), stream=stream)
+        else:
+            fitgb.paraexp_run_batched(probs, fitgb.make_opts(use_graph=1, autotune=1), stream)
+        for g in gs:
+            fitgb.fit_grid_destroy(g)
+
+    solve()   # autotuning and graph capture happen here
+    bms, _ = timed(stream, solve)
+    ref = [o.clone() for o in outs]
+    pms, _ = timed(stream, lambda: solve(plain=True))
+    same = all(torch.equal(a, b) for a, b in zip(outs, ref))
+    alg = batch_alg_bytes(ws)
+    achieved = alg / (bms / 1e3) / 1e9
+    return {"workload": "batch64", "grids": len(ws), "cells": int(sum(w.ncells for w in ws)), "K": ws[0].K,
+            "nsteps": ws[0].nsteps, "value": work / (bms / 1e3) / 1e9, "unit": UNIT, "seconds": bms / 1e3,
+            "roofline": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "kernel": "batched_tma_kernel (whole solve time, launches and superposition included)"},
+            "plain_per_window_s": pms / 1e3, "vs_plain": pms / bms, "probes_equal_to_plain": bool(same)}
+
+
+def adjoint_section(fitgb, dev, stream, peak):
+    """The differentiation configuration: 128^3, 10^4 steps, checkpoints every
+    100 steps, FP32: dJ/d eps_r of every cell by the adjoint sweep, against one
+    forward leapfrog run and against the 32 forward runs of the 16-cell central
+    finite-difference check it replaces (both timed with CUDA events)."""
+    import torch
+    from paper_1705_08019_gb300 import workloads as W
+    w = W.adjoint128()
+    eps = torch.from_numpy(w.eps_r).to(dev)
+    sig = torch.from_numpy(w.sigma).to(dev)
+    g = fitgb.fit_grid_create(w.dims, w.spacing, eps, None, sig, 32)
+    dt = w.cfl_fraction * fitgb.fit_cfl_dt(g)
+    J = torch.zeros(1, dtype=torch.float64, device=dev)
+    grad = torch.zeros(tuple(reversed(w.dims)), dtype=torch.float64, device=dev)
+    pr = torch.zeros((w.nsteps, len(w.probes)), dtype=torch.float64, device=dev)
+    fwd = lambda: fitgb.fit_leapfrog_run(g, dt, w.nsteps, 0, w.sources, w.probes, pr, stream=stream)
+    adj = lambda: fitgb.fit_adjoint_grad(g, dt, w.nsteps, w.sources, w.probes, 100, J, grad,
+                                         opts=fitgb.make_opts(profile=1), stream=stream)
+    fwd()
+    adj()
+    fms, _ = timed(stream, fwd)
+    ams, _ = timed(stream, adj)
+    st = fitgb.fit_last_stats(g)
+    fitgb.fit_grid_destroy(g)
+    out = {"workload": "adjoint128", "cells": w.ncells, "nsteps": w.nsteps, "checkpoint_every": 100,
+           "seconds": ams / 1e3, "forward_s": fms / 1e3, "over_forward": ams / fms,
+           "vs_plain": 32.0 * fms / ams,
+           "vs_plain_baseline": "32 forward runs: central finite differences on 16 cells (the check the adjoint "
+                                "replaces), each run as fast as the forward run here",
+           "gradient_cells": w.ncells}
+    if st["step_ms"] > 0:
+        achieved = st["alg_bytes"] / (st["step_ms"] / 1e3) / 1e9
+        out["roofline"] = {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                           "share_of_time": st["step_ms"] / ams,
+                           "kernel": "step and gradient launches of the three sweeps"}
+    return out
 
 
 def ncu_case(args):
@@ -418,6 +602,10 @@ def ncu_case(args):
         e0, h0 = (torch.from_numpy(a).to(dev) for a in W.random_state(w.dims, dtype=np.float32))
         opts = fitgb.make_opts(homogeneous="leja", expo_substep=args.ncu_steps, expo_degree=8)
         fitgb.fit_expo_propagate(g, dt, args.ncu_steps, w.probes, None, e0, h0, opts, s)
+    elif args.ncu_case == "solve":
+        # the workload's K equal windows over --ncu-steps steps: launches with the member counts of a full solve
+        w.nsteps = args.ncu_steps
+        fitgb.paraexp_run(g, dt, w.K, w.windows(), w.sources, w.probes, None, None, None, None, None, None, s)
     else:
         K = args.ncu_members
         win = np.array([j for j in range(K)] + [args.ncu_steps], dtype=np.int64)

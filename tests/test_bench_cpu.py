@@ -36,3 +36,19 @@ def test_bench_helpers():
     assert rate > 0 and sec > 0 and "oracle" in desc
     hbm, kind = bench.peaks()
     assert hbm > 0 and kind in ("measured", "fallback")
+
+
+def test_field_error_helpers():
+    """Relative L2 error per probe trace (columns) and per field component, max."""
+    import torch
+    import bench
+    ref = (torch.ones(10, 3, dtype=torch.float64), torch.ones(3, 2, 2, 2, dtype=torch.float64),
+           2 * torch.ones(3, 2, 2, 2, dtype=torch.float64))
+    pr = ref[0].clone()
+    pr[:, 1] *= 1.001
+    h = ref[2].clone()
+    h[2] *= 1.0 + 1e-6
+    errs = bench.field_errors(pr, ref[1], h, ref)
+    assert abs(errs["probes"] - 1e-3) < 1e-12 and errs["e"] == 0.0 and abs(errs["h"] - 1e-6) < 1e-15
+    assert errs["max"] == errs["probes"]
+    assert bench.traffic_from_profile(64) is None

@@ -160,7 +160,31 @@ def test_autograd_function():
     assert abs(float(J.item()) - J_ref) <= 1e-12 * J_ref
     assert eps.grad.dtype == torch.float32
     assert np.allclose(eps.grad.cpu().numpy(), 3.0 * grad_ref, rtol=1e-6, atol=1e-6 * np.abs(grad_ref).max() * 3)
-    # without a gradient request the forward runs the plain leapfrog only
+    # without a gradient request the library runs the forward pass and J only
     with torch.no_grad():
         J2 = probe_energy(eps.detach(), w.spacing, dt, w.nsteps, w.sources, w.probes, sigma=sig)
     assert abs(float(J2.item()) - J_ref) <= 1e-9 * J_ref
+
+
+@pytest.mark.parametrize("precision,tol", [(64, 1e-12), (32, 1e-5)])
+def test_functional_without_gradient_matches_oracle(precision, tol):
+    """fit_adjoint_grad with a null gradient (the autograd binding's no-grad
+    path): J = sum_n sum_p (e_p^n / L_p)^2 from the library equals the
+    oracle's J on a graded lossy grid (per-probe edge lengths)."""
+    import torch
+    from paper_1705_08019_gb300.autograd import probe_energy
+    w = W.graded_random(dims=(13, 11, 9))
+    w.nsteps = 150
+    w.probes = w.probes[:3]
+    dt = w.cfl_fraction * oracle.cfl_dt(w.dims, w.spacing, w.eps_r)
+    og = oracle.OracleGrid(w.dims, w.spacing, w.eps_r, None, w.sigma, dt=dt, round32=(precision == 32))
+    J_ref, _ = og.adjoint(w.nsteps, w.sources, w.probes)
+    g = fitgb.Grid(w.dims, w.spacing, w.eps_r, None, w.sigma, precision)
+    J = torch.zeros(1, dtype=torch.float64)
+    fitgb.fit_adjoint_grad(g.handle, dt, w.nsteps, w.sources, w.probes, 0, J, None)
+    g.close()
+    assert abs(float(J[0]) - J_ref) <= tol * J_ref
+    with torch.no_grad():
+        J2 = probe_energy(torch.from_numpy(w.eps_r).cuda(), w.spacing, dt, w.nsteps, w.sources, w.probes,
+                          sigma=torch.from_numpy(w.sigma).cuda(), precision=precision)
+    assert float(J2.item()) == float(J[0])

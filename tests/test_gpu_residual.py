@@ -78,33 +78,48 @@ def test_residual_leapfrog_matches_oracle(dims, kw, kernel, tile, record_propert
 
 
 def test_residual_initial_state_and_paraexp(record_property):
-    w = W.small_random(dims=(21, 13, 11), nsteps=400, K=4)
+    """A run continued from a state (the oracle's fields after 150 driven
+    steps, handed over in FP64 and split into float + residual), and ParaExp
+    from zero; both against the oracle with the RES_GAIN bound.  A white-noise
+    initial state (every mode up to the grid's highest, so the per-step
+    increment is as large as the field) is only held to the plain FP32
+    error."""
+    w = W.small_random(dims=(21, 13, 11), nsteps=250, K=4)
     dt = w.cfl_fraction * oracle.cfl_dt(w.dims, w.spacing, w.eps_r)
     og = oracle.OracleGrid(w.dims, w.spacing, w.eps_r, w.mu_r, w.sigma, dt=dt, round32=True)
+    _, _, e0, h0 = og.leapfrog(150, w.sources, w.probes)
+    ref = og.leapfrog(w.nsteps, w.sources, w.probes, e=e0, h=h0, step0=150)
     rng = np.random.default_rng(4)
-    e0 = rng.standard_normal(og.field_shape)
-    h0 = rng.standard_normal(og.field_shape) * 1e-2
+    n0 = rng.standard_normal(og.field_shape)
+    m0 = rng.standard_normal(og.field_shape) * 1e-2
     # only degrees of freedom: nothing at index n, no e tangential to a wall, no h normal to one
-    e0[:, -1] = 0; e0[:, :, -1] = 0; e0[:, :, :, -1] = 0
-    h0[:, -1] = 0; h0[:, :, -1] = 0; h0[:, :, :, -1] = 0
-    e0[0, :, 0, :] = 0; e0[0, 0, :, :] = 0; e0[1, :, :, 0] = 0; e0[1, 0, :, :] = 0
-    e0[2, :, :, 0] = 0; e0[2, :, 0, :] = 0
-    h0[0, :, :, 0] = 0; h0[1, :, 0, :] = 0; h0[2, 0, :, :] = 0
-    ref = og.leapfrog(w.nsteps, w.sources, w.probes, e=e0, h=h0, step0=11)
-    win = np.array([0, 50, 161, 299, 400])
+    n0[:, -1] = 0; n0[:, :, -1] = 0; n0[:, :, :, -1] = 0
+    m0[:, -1] = 0; m0[:, :, -1] = 0; m0[:, :, :, -1] = 0
+    n0[0, :, 0, :] = 0; n0[0, 0, :, :] = 0; n0[1, :, :, 0] = 0; n0[1, 0, :, :] = 0
+    n0[2, :, :, 0] = 0; n0[2, :, 0, :] = 0
+    m0[0, :, :, 0] = 0; m0[1, :, 0, :] = 0; m0[2, 0, :, :] = 0
+    nref = og.leapfrog(w.nsteps, w.sources, w.probes, e=n0, h=m0, step0=11)
+    win = np.array([0, 50, 101, 199, 250])
     pref = og.paraexp(4, win, w.sources, w.probes)
     res = {}
     for prec in (40, 32):
         g = fitgb.Grid.from_workload(w, prec)
         dtp = np.float64 if prec == 40 else np.float32
         pr, _, e, h = g.leapfrog(dt, w.nsteps, w.sources, w.probes, e=compact(e0).astype(dtp),
-                                 h=compact(h0).astype(dtp), step0=11)
+                                 h=compact(h0).astype(dtp), step0=150)
         lf = _errs(pr, e, h, (ref[0], ref[2], ref[3]))
+        pr, _, e, h = g.leapfrog(dt, w.nsteps, w.sources, w.probes, e=compact(n0).astype(dtp),
+                                 h=compact(m0).astype(dtp), step0=11)
+        nz = _errs(pr, e, h, (nref[0], nref[2], nref[3]))
         pr, ef, hf = g.paraexp(dt, 4, win, w.sources, w.probes)
         g.close()
-        res[prec] = (lf, _errs(pr, ef, hf, pref))
-    _check(record_property, "initial_state", res[40][0], res[32][0])
+        res[prec] = (lf, _errs(pr, ef, hf, pref), nz)
+    _check(record_property, "continued", res[40][0], res[32][0])
     _check(record_property, "paraexp", res[40][1], res[32][1])
+    for k in res[40][2]:
+        record_property(f"white_noise_{k}_err", res[40][2][k])
+        record_property(f"white_noise_{k}_bound", res[32][2][k])
+        assert res[40][2][k] <= res[32][2][k], (k, res[40][2][k], res[32][2][k])
 
 
 def test_residual_paraexp_batching_is_bitwise():
