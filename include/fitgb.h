@@ -35,7 +35,9 @@
  *   for FP32 and double otherwise.  Probe traces,
  *   energies, superposed fields, J and gradients are always double.
  * Pointers: every array argument may be a host or a device pointer; the
- *   library finds out with cudaPointerGetAttributes.  The caller owns all
+ *   library finds out with cudaPointerGetAttributes.  Device pointers must
+ *   be memory of the current device (or managed memory): memory of another
+ *   GPU gives FIT_ERR_ARG.  The caller owns all
  *   argument buffers; the library owns the grid and its device workspaces.
  * Streams: work is enqueued on `stream` (a cudaStream_t, NULL = legacy
  *   default stream).  A call whose outputs include a host pointer returns
@@ -388,9 +390,11 @@ int fit_last_stats(const fit_grid *g, fit_run_stats *out);
  * Every workspace lives in one fixed __device__ array of about 30 MiB held
  * by each GPU that loads the library until the process exits, so grids are
  * limited to ceil4(nx)*ny*nz <= 393216 cells (e.g. 64 x 64 x 96); larger
- * grids, more than 8 sources or 32 probes, or host pointers give
- * FIT_ERR_ARG.  The first call on a device looks the array up
- * (cudaGetSymbolAddress) and should come before any stream capture.  All
+ * grids, more than 8 sources or 32 probes, host pointers or pointers to
+ * another GPU's memory, and non-finite spacings or dt give FIT_ERR_ARG.
+ * Every call looks the array's address up on the current device
+ * (cudaGetSymbolAddress); the first call on a device also loads the
+ * library's device code there and should come before any stream capture.  All
  * calls share the array: calls whose work overlaps on the GPU race on it and
  * must be serialized by the caller.  Returns after the run has finished
  * (FIT_ERR_CFL / FIT_ERR_NONFINITE as fit_leapfrog_run). */
@@ -398,6 +402,13 @@ int fit_leapfrog_run_static(int nx, int ny, int nz, double dx, double dy, double
                             const float *eps_r, const float *sigma, double dt, long nsteps, long step0,
                             const fit_source *src, int nsrc, const fit_probe *prb, int nprb,
                             double *probe_out, float *e_io, float *h_io, void *stream);
+
+/* Test hook for the out-of-memory paths: the device allocation `after`
+ * allocations from now (0 = the next one) fails as if the device were out of
+ * memory, without calling cudaMalloc; every other allocation is made
+ * normally.  A negative value turns the hook off.  The failing call returns
+ * FIT_ERR_OOM and leaves its grid usable.  The paper has no counterpart. */
+int fit_debug_fail_alloc(long long after);
 
 /* Wait for the grid's outstanding work on `stream` and return the first
  * deferred device error, if any. */

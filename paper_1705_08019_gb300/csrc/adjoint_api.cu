@@ -230,6 +230,7 @@ int fit_adjoint_grad(fit_grid *g, double dt, long nsteps, const fit_source *src,
                      int nprb, int ckpt_every, double *J_out, double *grad_eps_r, const fit_run_opts *opts,
                      void *stream) {
     if (!g || nsteps < 1 || ckpt_every < 0) return FIT_ERR_ARG;
+    if (any_foreign({J_out, grad_eps_r})) return FIT_ERR_ARG;
     int rc;
     if ((rc = check_dt(g, dt, opts))) return rc;
     if ((rc = check_sources_probes(g, src, nsrc, prb, nprb))) return rc;

@@ -12,11 +12,31 @@
 // last step, shortest member first; its probe rows go to a buffer of its own
 // and are summed in member order at the end, so the result does not depend
 // on scheduling.
+#include <atomic>
+
 #include "grid.h"
 
 using namespace fitgb;
 
 namespace fitgb {
+
+namespace {
+std::atomic<long long> g_fail_alloc{-1};   // allocations left before the injected failure (-1: off)
+}
+
+cudaError_t dev_alloc(void **p, size_t bytes) {
+    long long left = g_fail_alloc.load();
+    while (left >= 0) {
+        if (g_fail_alloc.compare_exchange_weak(left, left - 1)) {
+            if (left == 0) {   // this is the allocation chosen to fail
+                *p = nullptr;
+                return cudaErrorMemoryAllocation;
+            }
+            break;
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
 
 // Run `specs` members, iteration-aligned; see the file comment.
 //   probe_dev: (probe rows) x nprb device buffer to receive the probe sum, or null
@@ -535,6 +555,7 @@ int fit_grid_create(int nx, int ny, int nz, double dx, double dy, double dz, con
     *out = nullptr;
     if (nx < 1 || ny < 1 || nz < 1 || !eps_r) return FIT_ERR_ARG;
     if (flags & ~FIT_FLAG_COEF_FLOAT) return FIT_ERR_ARG;
+    if (any_foreign({eps_r, mu_r, sigma})) return FIT_ERR_ARG;
     if (!(dx > 0) || !(dy > 0) || !(dz > 0) || !std::isfinite(dx) || !std::isfinite(dy) || !std::isfinite(dz))
         return FIT_ERR_ARG;
     if (precision != 32 && precision != 64 && precision != 48 && precision != 40) return FIT_ERR_ARG;
@@ -555,14 +576,15 @@ int fit_grid_create(int nx, int ny, int nz, double dx, double dy, double dz, con
         fit_grid_destroy(g);
         return rc;
     };
-    if (cudaMalloc(&g->eps, bytes) != cudaSuccess) { cudaGetLastError(); return fail(FIT_ERR_OOM); }
+    cudaError_t ae;
+    if ((ae = dev_alloc((void **)&g->eps, bytes)) != cudaSuccess) { cudaGetLastError(); return fail(map_err(ae)); }
     if (cudaMemcpy(g->eps, eps_r, bytes, kind_to_dev(eps_r)) != cudaSuccess) return fail(FIT_ERR_CUDA);
     if (mu_r) {
-        if (cudaMalloc(&g->mu, bytes) != cudaSuccess) { cudaGetLastError(); return fail(FIT_ERR_OOM); }
+        if ((ae = dev_alloc((void **)&g->mu, bytes)) != cudaSuccess) { cudaGetLastError(); return fail(map_err(ae)); }
         if (cudaMemcpy(g->mu, mu_r, bytes, kind_to_dev(mu_r)) != cudaSuccess) return fail(FIT_ERR_CUDA);
     }
     if (sigma) {
-        if (cudaMalloc(&g->sig, bytes) != cudaSuccess) { cudaGetLastError(); return fail(FIT_ERR_OOM); }
+        if ((ae = dev_alloc((void **)&g->sig, bytes)) != cudaSuccess) { cudaGetLastError(); return fail(map_err(ae)); }
         if (cudaMemcpy(g->sig, sigma, bytes, kind_to_dev(sigma)) != cudaSuccess) return fail(FIT_ERR_CUDA);
     }
     if (ensure(g->scratch, 64)) return fail(FIT_ERR_OOM);
@@ -648,6 +670,7 @@ int fit_leapfrog_run(fit_grid *g, double dt, long nsteps, long step0, const fit_
                      const fit_probe *prb, int nprb, double *probe_out, double *energy_out, void *e_io, void *h_io,
                      const fit_run_opts *opts, void *stream) {
     if (!g || nsteps < 0) return FIT_ERR_ARG;
+    if (any_foreign({probe_out, energy_out, e_io, h_io})) return FIT_ERR_ARG;
     int rc;
     if ((rc = check_dt(g, dt, opts))) return rc;
     if ((rc = check_sources_probes(g, src, nsrc, prb, nprb))) return rc;
@@ -666,6 +689,7 @@ int paraexp_run(fit_grid *g, double dt, int K, const long *win, const fit_source
                 const fit_probe *prb, int nprb, double *probe_out, double *e_final, double *h_final,
                 const void *e0, const void *h0, const fit_run_opts *opts, void *stream) {
     if (!g || K < 1 || !win) return FIT_ERR_ARG;
+    if (any_foreign({probe_out, e_final, h_final, e0, h0})) return FIT_ERR_ARG;
     for (int j = 1; j <= K; ++j)
         if (win[j] <= win[j - 1]) return FIT_ERR_ARG;
     int rc;
@@ -694,6 +718,11 @@ int paraexp_run(fit_grid *g, double dt, int K, const long *win, const fit_source
 int fit_last_stats(const fit_grid *g, fit_run_stats *out) {
     if (!g || !out) return FIT_ERR_ARG;
     *out = g->stats;
+    return FIT_OK;
+}
+
+int fit_debug_fail_alloc(long long after) {
+    g_fail_alloc.store(after < 0 ? -1 : after);
     return FIT_OK;
 }
 

@@ -1,8 +1,12 @@
 // batched_api.cu -- paraexp_run_batched: many ParaExp problems of uneven
 // size in one persistent, graph-captured, autotuned launch per iteration
 // (kernel batched_tma_kernel in step_tma.cuh).
+#include <cstdio>
+#include <cstdlib>
+#include <fstream>
 #include <map>
 #include <mutex>
+#include <sstream>
 #include <string>
 
 #include "grid.h"
@@ -18,6 +22,54 @@ namespace {
 
 std::mutex g_tune_mu;
 std::map<std::string, Tile> g_tune_cache;   // batch signature -> tile, kz
+
+// Optional on-disk copy of the autotuner's choices, shared across processes:
+// the file named by the environment variable FITGB_TUNE_CACHE holds one line
+// per choice, "<device>|<signature> tx ty kz stages"; a later line for the
+// same key wins, and lines that do not parse are ignored.
+std::string tune_device_name() {
+    int d = 0;
+    cudaDeviceProp p;
+    if (cudaGetDevice(&d) != cudaSuccess || cudaGetDeviceProperties(&p, d) != cudaSuccess) {
+        cudaGetLastError();
+        return "unknown";
+    }
+    std::string n = p.name;
+    for (char &c : n)
+        if (c == ' ' || c == '|') c = '_';
+    return n;
+}
+
+bool tune_disk_lookup(const std::string &key, Tile *out) {
+    const char *path = std::getenv("FITGB_TUNE_CACHE");
+    if (!path || !*path) return false;
+    std::ifstream f(path);
+    if (!f) return false;
+    std::string line;
+    bool found = false;
+    while (std::getline(f, line)) {
+        std::istringstream in(line);
+        std::string k;
+        Tile t = {0, 0, 0, 2, 0};
+        if (!(in >> k >> t.tx >> t.ty >> t.kz >> t.stages) || k != key) continue;
+        if (!batched_tile_supported(t.tx, t.ty) || t.kz < 1 || (t.stages != 3 && t.stages != 4)) continue;
+        *out = t;
+        found = true;
+    }
+    return found;
+}
+
+void tune_disk_store(const std::string &key, const Tile &t) {
+    const char *path = std::getenv("FITGB_TUNE_CACHE");
+    if (!path || !*path) return;
+    char line[512];
+    const int n = std::snprintf(line, sizeof(line), "%s %d %d %d %d\n", key.c_str(), t.tx, t.ty, t.kz, t.stages);
+    if (n <= 0 || n >= (int)sizeof(line)) return;
+    if (FILE *f = std::fopen(path, "a")) {   // one short append per choice
+        std::fwrite(line, 1, (size_t)n, f);
+        std::fclose(f);
+    }
+}
 
 struct BatchHost {
     const fit_paraexp_problem *p = nullptr;
@@ -172,8 +224,8 @@ int batched_group(const std::vector<const fit_paraexp_problem *> &probs, bool lo
     std::vector<WorkItem> items;
     DevBuf d_grids, d_maps, d_items, d_counter;
     const size_t gd_bytes = sizeof(GridDesc<float>) * ng, map_bytes = sizeof(CUtensorMap) * 2 * ng;
-    if (cudaMalloc(&d_grids.p, gd_bytes) != cudaSuccess || cudaMalloc(&d_maps.p, map_bytes) != cudaSuccess ||
-        cudaMalloc(&d_counter.p, sizeof(int) * (size_t)std::max<long long>(nit_max, 8)) != cudaSuccess) {
+    if (dev_alloc(&d_grids.p, gd_bytes) != cudaSuccess || dev_alloc(&d_maps.p, map_bytes) != cudaSuccess ||
+        dev_alloc(&d_counter.p, sizeof(int) * (size_t)std::max<long long>(nit_max, 8)) != cudaSuccess) {
         cudaGetLastError();
         return FIT_ERR_OOM;
     }
@@ -185,7 +237,7 @@ int batched_group(const std::vector<const fit_paraexp_problem *> &probs, bool lo
         if (items.size() > items_cap) {
             if (d_items.p) cudaFree(d_items.p);
             d_items.p = nullptr;
-            if (cudaMalloc(&d_items.p, sizeof(WorkItem) * items.size()) != cudaSuccess) {
+            if (dev_alloc(&d_items.p, sizeof(WorkItem) * items.size()) != cudaSuccess) {
                 cudaGetLastError();
                 return FIT_ERR_OOM;
             }
@@ -218,18 +270,22 @@ int batched_group(const std::vector<const fit_paraexp_problem *> &probs, bool lo
 
     // autotune: time a few iterations of each candidate, once per batch signature
     if (opts && opts->autotune && !(opts->tile_x > 0)) {
-        std::string sig = lossy ? "L" : "N";
+        std::string sig = std::string("fp32") + (lossy ? "L" : "N");
         for (int gi = 0; gi < ng; ++gi) {
             const fit_grid *g = H[gi].p->grid;
             sig += ":" + std::to_string(g->nx) + "x" + std::to_string(g->ny) + "x" + std::to_string(g->nz) + "k" +
                    std::to_string(H[gi].p->K);
         }
+        const std::string key = tune_device_name() + "|" + sig;
         bool hit = false;
         {
             std::lock_guard<std::mutex> lock(g_tune_mu);
-            auto f = g_tune_cache.find(sig);
+            auto f = g_tune_cache.find(key);
             if (f != g_tune_cache.end()) {
                 tile = f->second;
+                hit = true;
+            } else if (tune_disk_lookup(key, &tile)) {
+                g_tune_cache[key] = tile;
                 hit = true;
             }
         }
@@ -262,7 +318,8 @@ int batched_group(const std::vector<const fit_paraexp_problem *> &probs, bool lo
             cudaEventDestroy(e1);
             tile = best_t;
             std::lock_guard<std::mutex> lock(g_tune_mu);
-            g_tune_cache[sig] = tile;
+            g_tune_cache[key] = tile;
+            tune_disk_store(key, tile);
             // the trial steps wrote into the states and probe rows: start over from zero
             for (int gi = 0; gi < ng; ++gi) {
                 fit_grid *g = H[gi].p->grid;
@@ -361,6 +418,7 @@ int paraexp_run_batched(const fit_paraexp_problem *probs, int nprobs, const fit_
     for (int p = 0; p < nprobs; ++p) {
         const fit_paraexp_problem &q = probs[p];
         if (!q.grid || q.K < 1 || !q.win) return FIT_ERR_ARG;
+        if (any_foreign({q.probe_out, q.e_final, q.h_final})) return FIT_ERR_ARG;
         for (int j = 1; j <= q.K; ++j)
             if (q.win[j] <= q.win[j - 1]) return FIT_ERR_ARG;
         int rc;

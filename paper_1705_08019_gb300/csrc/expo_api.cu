@@ -459,6 +459,7 @@ int fit_spectral_bound(const fit_grid *g, double *beta) {
 int fit_expo_propagate(fit_grid *g, double dt, long nsteps, const fit_probe *prb, int nprb, double *probe_out,
                        void *e_io, void *h_io, const fit_run_opts *opts, void *stream) {
     if (!g || nsteps < 0 || !opts || !(dt > 0.0) || !std::isfinite(dt)) return FIT_ERR_ARG;
+    if (any_foreign({probe_out, e_io, h_io})) return FIT_ERR_ARG;
     if (opts->homogeneous != FIT_HOMOG_LEJA && opts->homogeneous != FIT_HOMOG_TAYLOR) return FIT_ERR_ARG;
     int rc;
     if ((rc = check_sources_probes(g, nullptr, 0, prb, nprb))) return rc;

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <initializer_list>
 #include <new>
 #include <vector>
 
@@ -67,13 +68,18 @@ inline int map_err(cudaError_t e) {
         }                                                        \
     } while (0)
 
+// Every device allocation of the library goes through dev_alloc.  The test
+// hook fit_debug_fail_alloc makes one chosen allocation fail as if the device
+// were out of memory, without calling cudaMalloc.
+cudaError_t dev_alloc(void **p, size_t bytes);
+
 inline int ensure(Buf &b, size_t bytes) {
     if (bytes == 0) bytes = 16;
     if (b.n >= bytes) return FIT_OK;
     if (b.p) cudaFree(b.p);
     b.p = nullptr;
     b.n = 0;
-    cudaError_t e = cudaMalloc(&b.p, bytes);
+    cudaError_t e = dev_alloc(&b.p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         b.p = nullptr;
@@ -97,6 +103,30 @@ inline bool is_device(const void *p) {
         return false;
     }
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// true if p is device memory of a GPU other than the current one: the
+// library's kernels cannot dereference it, so entry points reject it
+inline bool foreign_device(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (at.type != cudaMemoryTypeDevice) return false;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return at.device != dev;
+}
+
+inline bool any_foreign(std::initializer_list<const void *> ps) {
+    for (const void *p : ps)
+        if (foreign_device(p)) return true;
+    return false;
 }
 
 inline cudaMemcpyKind kind_to_dev(const void *src) {

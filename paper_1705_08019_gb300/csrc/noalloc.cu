@@ -11,17 +11,18 @@
 // in one file-scope __device__ array of kStaticScratchBytes (about 30 MiB)
 // that every GPU loading this library holds until the process exits.
 //
-// Its address is looked up once per device with cudaGetSymbolAddress (host
-// code cannot use the array's name as a device address); that set-up happens
-// in the first call on each device, which should therefore come before any
-// stream capture.  All calls share the one array and it keeps the last
+// Its device address is looked up with cudaGetSymbolAddress at the start of
+// every call, on the current device (host code cannot use the array's name
+// as a device address, and a cached address would be stale after the
+// caller's context is torn down and recreated); the first call on a device
+// also makes the runtime load this library's device code there, so it should
+// come before any stream capture.  All calls share the one array and it keeps the last
 // call's contents: this file clears and rebuilds everything a run reads
 // before using it, and calls whose work overlaps on the GPU (different
 // streams, or different threads) race on it and must be serialized by the
 // caller.
 #include <cmath>
 #include <cstring>
-#include <mutex>
 
 #include "internal.h"
 
@@ -47,34 +48,30 @@ constexpr size_t kStaticScratchBytes = align_up(kFlagsOff + 64);
 
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-unsigned char *g_scratch_ptr[kMaxDevices] = {};
-
-// The device address of the scratch array on the current device (looked up
-// once per device); null on failure.
+// The device address of the scratch array on the current device; null on failure.
 unsigned char *scratch_on_current_device() {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return nullptr;
-        }
-        g_scratch_ptr[dev] = static_cast<unsigned char *>(p);
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return nullptr;
     }
-    return g_scratch_ptr[dev];
+    return static_cast<unsigned char *>(p);
 }
 
+// device memory of the current device, or managed memory
 bool on_device(const void *p) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 int status_of(cudaError_t e) {
@@ -93,6 +90,7 @@ extern "C" int fit_leapfrog_run_static(int nx, int ny, int nz, double dx, double
                                        int nprb, double *probe_out, float *e_io, float *h_io, void *stream) {
     if (nx < 1 || ny < 1 || nz < 1 || nsteps < 0) return FIT_ERR_ARG;
     if (!(dx > 0) || !(dy > 0) || !(dz > 0) || !(dt > 0)) return FIT_ERR_ARG;
+    if (!std::isfinite(dx) || !std::isfinite(dy) || !std::isfinite(dz) || !std::isfinite(dt)) return FIT_ERR_ARG;
     const int pitch = pitch_of(nx);
     const long long ncp = (long long)pitch * ny * nz;
     if (ncp > kStaticCells) return FIT_ERR_ARG;   // beyond the fixed scratch

@@ -35,7 +35,7 @@ HOMOG = {"leapfrog": HOMOG_LEAPFROG, "leja": HOMOG_LEJA, "taylor": HOMOG_TAYLOR}
 EXPORTED = ("fit_grid_create", "fit_grid_destroy", "fit_cfl_dt", "fit_grid_info", "fit_leapfrog_run",
             "paraexp_run", "paraexp_run_batched", "fit_adjoint_grad", "fit_sync", "fit_strerror",
             "fit_version", "fit_last_stats", "fit_leapfrog_run_static", "fit_expo_plan", "fit_expo_coeffs",
-            "fit_expo_propagate", "fit_grid_create_graded", "fit_spectral_bound")
+            "fit_expo_propagate", "fit_grid_create_graded", "fit_spectral_bound", "fit_debug_fail_alloc")
 
 
 class FitError(RuntimeError):
@@ -125,12 +125,20 @@ def load():
         lib.fit_last_stats.restype = I
         lib.fit_sync.argtypes = [P, P]
         lib.fit_sync.restype = I
+        lib.fit_debug_fail_alloc.argtypes = [ctypes.c_longlong]
+        lib.fit_debug_fail_alloc.restype = I
         lib.fit_strerror.argtypes = [I]
         lib.fit_strerror.restype = ctypes.c_char_p
         lib.fit_version.argtypes = []
         lib.fit_version.restype = ctypes.c_char_p
         _lib = lib
         return lib
+
+
+def fit_debug_fail_alloc(after: int):
+    """Test hook: the device allocation `after` allocations from now fails as
+    out of memory (negative: off)."""
+    _check(load().fit_debug_fail_alloc(int(after)), "fit_debug_fail_alloc")
 
 
 def strerror(status: int) -> str:

@@ -48,3 +48,39 @@ def test_product_path_does_not_import_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "fit_oracle" not in text, f
+
+
+def test_injected_allocation_failure_gives_oom():
+    """The allocator hook fails the first device allocation of fit_grid_create
+    before cudaMalloc is reached: FIT_ERR_OOM with no GPU involved, the grid
+    handle stays null, and the hook is one-shot."""
+    import ctypes
+    import numpy as np
+    from paper_1705_08019_gb300 import build, fitgb
+    try:
+        build.nvcc()
+    except RuntimeError:
+        pytest.skip("nvcc not available")
+    build.build()
+    lib = fitgb.load()
+    eps = np.ones((4, 5, 6), np.float32)
+    out = ctypes.c_void_p(0)
+    # control: without the hook the call either succeeds (a GPU is present) or
+    # fails in the CUDA runtime (FIT_ERR_CUDA: no device), never with OOM
+    rc = lib.fit_grid_create(6, 5, 4, 1e-3, 1e-3, 1e-3, eps.ctypes.data_as(ctypes.c_void_p), None, None, 32, 0,
+                             ctypes.byref(out))
+    if rc == fitgb.FIT_OK:
+        lib.fit_grid_destroy(out)
+        out = ctypes.c_void_p(0)
+    else:
+        assert rc == fitgb.FIT_ERR_CUDA
+    fitgb.fit_debug_fail_alloc(0)
+    try:
+        rc = lib.fit_grid_create(6, 5, 4, 1e-3, 1e-3, 1e-3, eps.ctypes.data_as(ctypes.c_void_p), None, None, 32, 0,
+                                 ctypes.byref(out))
+    finally:
+        fitgb.fit_debug_fail_alloc(-1)
+    assert rc == fitgb.FIT_ERR_OOM
+    assert out.value is None
+    assert fitgb.strerror(rc) == "device out of memory"
+

@@ -148,3 +148,50 @@ def test_batched_with_leja_homogeneous_problems():
     assert_same(run_problems(ws, batched=True, opts=opts), ref)
     lf = run_problems(ws, batched=False)
     assert not np.array_equal(ref[0][0], lf[0][0])   # not the leapfrog result
+
+
+def test_autotune_disk_cache(tmp_path):
+    """FITGB_TUNE_CACHE keeps the autotuner's choice in a file keyed by device
+    name and batch signature (precision, loss, every grid's dims and K): a
+    tuned run appends one line; a fresh process that finds the line (and a
+    line it cannot parse) skips the tuning and gives the same bits."""
+    import json
+    import os
+    import subprocess
+    import sys
+    path = tmp_path / "tune.txt"
+    os.environ["FITGB_TUNE_CACHE"] = str(path)
+    try:
+        ws = make_batch()[:3]
+        a = run_problems(ws, True, fitgb.make_opts(autotune=1))
+    finally:
+        del os.environ["FITGB_TUNE_CACHE"]
+    lines = path.read_text().splitlines()
+    assert len(lines) == 2   # the lossless and the lossy problems are tuned as two groups
+    sigs = []
+    for line in lines:
+        key, tx, ty, kz, st = line.split()
+        dev, sig = key.split("|")
+        assert "GB300" in dev and sig.startswith("fp32")
+        assert int(st) in (3, 4) and int(kz) >= 1
+        sigs.append(sig)
+    for w in ws:
+        nx, ny, nz = w.dims
+        tag = ("fp32L" if w.sigma is not None else "fp32N")
+        assert any(s.startswith(tag) and f"{nx}x{ny}x{nz}k{w.K}" in s for s in sigs)
+    n_lines = len(lines)
+    with open(path, "a") as f:
+        f.write("not a tile line\n")
+    code = ("import sys, json, numpy as np; sys.path[:0] = [%r, %r]\n"
+            "import test_gpu_batched as t\nfrom paper_1705_08019_gb300 import fitgb\n"
+            "out = t.run_problems(t.make_batch()[:3], True, fitgb.make_opts(autotune=1))\n"
+            "print(json.dumps([[x.tolist() for x in o] for o in out]))\n") % (
+        os.path.dirname(os.path.dirname(os.path.abspath(__file__))), os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, FITGB_TUNE_CACHE=str(path))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    b = json.loads(r.stdout.strip().splitlines()[-1])
+    for oa, ob in zip(a, b):
+        for x, y in zip(oa, ob):
+            assert np.array_equal(x, np.array(y))
+    assert len(path.read_text().splitlines()) == n_lines + 1   # nothing tuned, nothing appended

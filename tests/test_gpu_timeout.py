@@ -70,3 +70,33 @@ def test_fused_leja_pair_timeout_and_recovery():
     g.close()
     for a, b in zip(again, ref):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("nth", [0, 1, 2, 3, 5, 8])
+def test_injected_oom_reports_and_grid_recovers(nth):
+    """The allocator hook fails the nth device allocation of a ParaExp call on
+    a fresh grid (coefficients, states, probe rows, sources, ...): the call
+    returns FIT_ERR_OOM (or succeeds if it makes fewer allocations), and the
+    same grid then reproduces the reference bit for bit."""
+    w = W.small_random(dims=(19, 13, 11), nsteps=40, K=3)
+    g0 = fitgb.Grid.from_workload(w, 32)
+    dt = 0.9 * g0.cfl_dt()
+    win = w.windows()
+    ref = g0.paraexp(dt, w.K, win, w.sources, w.probes)
+    g0.close()
+    g = fitgb.Grid.from_workload(w, 32)
+    fitgb.fit_debug_fail_alloc(nth)
+    try:
+        g.paraexp(dt, w.K, win, w.sources, w.probes)
+        failed = False
+    except fitgb.FitError as e:
+        assert e.status == fitgb.FIT_ERR_OOM
+        failed = True
+    finally:
+        fitgb.fit_debug_fail_alloc(-1)
+    out = g.paraexp(dt, w.K, win, w.sources, w.probes)
+    g.close()
+    for a, b in zip(out, ref):
+        assert np.array_equal(a, b)
+    if nth == 0:
+        assert failed
