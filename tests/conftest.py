@@ -14,3 +14,12 @@ if HERE not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: longer CPU test")
+
+
+@pytest.fixture(autouse=True)
+def _record_tolerances(record_property):
+    """Let helpers.check record every compared error and its tolerance."""
+    import helpers
+    helpers.RECORD = record_property
+    yield
+    helpers.RECORD = None

@@ -12,27 +12,58 @@ import oracle
 # ~1e3 steps of O(10) flops each).
 TOL64 = 1e-11
 # FP32 paths are compared with the FP64 oracle run on the same float-rounded
-# coefficients.  The floor 1e-5 is the method's FP32 target.  Rounding every
-# stored e and h value to float accumulates over the steps like a random
-# walk (about 6e-8 sqrt(steps) of the field), and more in relative terms for a
-# quantity whose own norm is small; no FP32-storage scheme can beat the
-# "store32" model (exact arithmetic, every stored e and h rounded to float).
-# The tolerance is therefore max(1e-5, FP32_FACTOR x the store32 model's own
-# error) per compared quantity: FP32 arithmetic in the curl sums and updates
-# adds rounding of the same order (1.3-2.2x the model in a float32 numpy
-# emulation), and 4x leaves margin while a real indexing or coefficient bug
-# gives errors of order one.
+# coefficients.  Rounding every stored e and h value to float accumulates over
+# the steps like a random walk (about 6e-8 sqrt(steps) of the field), and more
+# in relative terms for a quantity whose own norm is small; the oracle's
+# "store32" model (exact arithmetic, every stored e and h rounded to float)
+# measures that part for each case.  FP32 arithmetic in the curl sums and the
+# updates adds rounding of the same order.  The tolerance of a quantity is
+# FACTOR x its store32-model error, FACTOR = 1.3 x the largest ratio GPU
+# error / model error observed on GB300 over the FP32 parity tests (fields and
+# probes: ratios 0.98 ... 3.07 over 75 quantities, median 1.40; energies: 0.47
+# ... 5.05 over 14); a real indexing or coefficient bug gives errors of order
+# one.  MODEL_FLOOR only keeps a zero model error from asking for bit equality.
+# TOL32 is the method's FP32 field-error target, for full-size runs.
 TOL32 = 1e-5
 FP32_FACTOR = 4.0
+ENERGY_FACTOR = 6.5
+MODEL_FLOOR = 1e-9
 
 
-def tol32(model, ref):
+# the current test's record_property (set by an autouse fixture in conftest.py)
+RECORD = None
+
+
+class Tol(float):
+    """An FP32 tolerance: its value, and the store32-model error it was derived from."""
+
+    def __new__(cls, value, model):
+        obj = float.__new__(cls, value)
+        obj.model = float(model)
+        return obj
+
+
+def tol32(model, ref, factor=FP32_FACTOR):
     """FP32 tolerance for one quantity from its store32-model value."""
-    return max(TOL32, FP32_FACTOR * relerr(model, ref))
+    m = relerr(model, ref)
+    return Tol(max(MODEL_FLOOR, factor * m), m)
 
 
 def tol32_probe(model, ref):
-    return max(TOL32, FP32_FACTOR * probe_relerr(model, ref))
+    m = probe_relerr(model, ref)
+    return Tol(max(MODEL_FLOOR, FP32_FACTOR * m), m)
+
+
+def check(name, err, tol):
+    """assert err <= tol, recording the achieved error, the tolerance and (for
+    FP32 tolerances) the model error as properties of the running test."""
+    err = float(err)
+    if RECORD is not None:
+        RECORD(f"{name}_err", err)
+        RECORD(f"{name}_tol", float(tol))
+        if isinstance(tol, Tol):
+            RECORD(f"{name}_model", tol.model)
+    assert err <= tol, (name, err, float(tol))
 
 
 def relerr(x, ref, floor=None):

@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import (TOL32, TOL64, canonical, compact, oracle_grid, probe_relerr, relerr, tol32,
+from helpers import (ENERGY_FACTOR, TOL32, TOL64, canonical, check, compact, oracle_grid, probe_relerr, relerr, tol32,
                      tol32_probe)
 from paper_1705_08019_gb300 import fitgb
 from paper_1705_08019_gb300 import workloads as W
@@ -51,7 +51,7 @@ def run_pair(w, nsteps, precision, scheme=0, energy=True, e0=None, h0=None, step
     if precision == 32:
         sg = oracle_grid(w, dt, round32=True, scheme=scheme, store32=True)
         mpr, men, me, mh = sg.leapfrog(nsteps, w.sources, w.probes, step0=step0, e=e0, h=h0, energy=energy)
-        tol = (tol32_probe(mpr, opr), tol32(men, oen) if energy else None, tol32(compact(me), ref[2]),
+        tol = (tol32_probe(mpr, opr), tol32(men, oen, ENERGY_FACTOR) if energy else None, tol32(compact(me), ref[2]),
                tol32(compact(mh), ref[3]))
     else:
         tol = (TOL64,) * 4
@@ -61,11 +61,11 @@ def run_pair(w, nsteps, precision, scheme=0, energy=True, e0=None, h0=None, step
 def check_pair(gpu, ref, tol):
     pr, en, e, h = gpu
     opr, oen, oe, oh = ref
-    assert probe_relerr(pr, opr) <= tol[0]
-    assert relerr(e, oe) <= tol[2]
-    assert relerr(h, oh) <= tol[3]
+    check("probes", probe_relerr(pr, opr), tol[0])
+    check("e", relerr(e, oe), tol[2])
+    check("h", relerr(h, oh), tol[3])
     if en is not None:
-        assert relerr(en, oen) <= tol[1]
+        check("en", relerr(en, oen), tol[1])
 
 
 def test_cfl_matches_oracle():
@@ -170,9 +170,9 @@ def test_paraexp_fp32_matches_oracle_and_modes_agree():
     opr, oef, ohf = og.paraexp(5, win, w.sources, w.probes)
     mpr, mef, mhf = oracle_grid(w, dt, round32=True, store32=True).paraexp(5, win, w.sources, w.probes)
     oef, ohf, mef, mhf = compact(oef), compact(ohf), compact(mef), compact(mhf)
-    assert probe_relerr(pr, opr) <= tol32_probe(mpr, opr)
-    assert relerr(ef, oef) <= tol32(mef, oef)
-    assert relerr(hf, ohf) <= tol32(mhf, ohf)
+    check("probes", probe_relerr(pr, opr), tol32_probe(mpr, opr))
+    check("ef", relerr(ef, oef), tol32(mef, oef))
+    check("hf", relerr(hf, ohf), tol32(mhf, ohf))
     # plain per-window runs (one member after another) give the same bits
     pr1, ef1, hf1 = g.paraexp(dt, 5, win, w.sources, w.probes, opts=fitgb.make_opts(members_per_pass=1))
     assert np.array_equal(pr, pr1) and np.array_equal(ef, ef1) and np.array_equal(hf, hf1)
@@ -181,7 +181,8 @@ def test_paraexp_fp32_matches_oracle_and_modes_agree():
     # compensated FP32 superposition stays within the FP32 tolerance
     pr3, ef3, hf3 = g.paraexp(dt, 5, win, w.sources, w.probes, opts=fitgb.make_opts(sum_mode=1))
     assert np.array_equal(pr, pr3)
-    assert relerr(ef3, oef) <= tol32(mef, oef) and relerr(hf3, ohf) <= tol32(mhf, ohf)
+    check("ef_kahan", relerr(ef3, oef), tol32(mef, oef))
+    check("hf_kahan", relerr(hf3, ohf), tol32(mhf, ohf))
     g.close()
 
 
@@ -209,9 +210,9 @@ def test_paraexp_with_initial_value(precision):
         tp, te, th = tol32_probe(mpr, opr), tol32(compact(mef), oef), tol32(compact(mhf), ohf)
     else:
         tp = te = th = TOL64
-    assert probe_relerr(pr, opr) <= tp
-    assert relerr(ef, oef) <= te
-    assert relerr(hf, ohf) <= th
+    check("probes", probe_relerr(pr, opr), tp)
+    check("ef", relerr(ef, oef), te)
+    check("hf", relerr(hf, ohf), th)
     g.close()
 
 
@@ -321,8 +322,8 @@ def test_fullsize_boxes256_light_cone():
     ge = e[:, ck - R:ck + R + 1, cj - R:cj + R + 1, ci - R:ci + R + 1]
     gh = h[:, ck - R:ck + R + 1, cj - R:cj + R + 1, ci - R:ci + R + 1]
     c3 = (slice(None), core, core, core)
-    assert relerr(ge[c3], oe[c3]) <= tol32(me[c3], oe[c3])
-    assert relerr(gh[c3], oh[c3]) <= tol32(mh[c3], oh[c3])
+    check("ge", relerr(ge[c3], oe[c3]), tol32(me[c3], oe[c3]))
+    check("gh", relerr(gh[c3], oh[c3]), tol32(mh[c3], oh[c3]))
     # outside the cone everything is still exactly zero
     mask = np.ones(e.shape[1:], bool)
     mask[ck - N - 1:ck + N + 2, cj - N - 1:cj + N + 2, ci - N - 1:ci + N + 2] = False
