@@ -50,6 +50,7 @@ def parse():
                          "[default: the workload's]")
     ap.add_argument("--nsteps", type=int, default=None, help="override the workload's step count")
     ap.add_argument("--kernel", type=int, default=0, help="opts.kernel of the solve [0 = the library's default]")
+    ap.add_argument("--tile-z", type=int, default=0, help="opts.tile_z (z planes per CTA) [0 = the library's default]")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -348,7 +349,7 @@ def run_ours(args, rank, world, local_rank):
         g = fitgb.fit_grid_create(w.dims, w.spacing, eps_d, mu_d, sig_d, precision or w.precision)
         fitgb.paraexp_run(g, dt, w.K, win, w.sources, w.probes, probe_d, ef_d, hf_d,
                           opts=fitgb.make_opts(profile=int(profile), members_per_pass=members_per_pass,
-                                               kernel=args.kernel),
+                                               kernel=args.kernel, tile_z=args.tile_z),
                           stream=stream)
         st = fitgb.fit_last_stats(g)
         fitgb.fit_grid_destroy(g)
@@ -542,12 +543,13 @@ def adjoint_section(fitgb, dev, stream, peak):
     grad = torch.zeros(tuple(reversed(w.dims)), dtype=torch.float64, device=dev)
     pr = torch.zeros((w.nsteps, len(w.probes)), dtype=torch.float64, device=dev)
     fwd = lambda: fitgb.fit_leapfrog_run(g, dt, w.nsteps, 0, w.sources, w.probes, pr, stream=stream)
-    adj = lambda: fitgb.fit_adjoint_grad(g, dt, w.nsteps, w.sources, w.probes, 100, J, grad,
-                                         opts=fitgb.make_opts(profile=1), stream=stream)
+    adj = lambda profile=0: fitgb.fit_adjoint_grad(g, dt, w.nsteps, w.sources, w.probes, 100, J, grad,
+                                                   opts=fitgb.make_opts(profile=profile), stream=stream)
     fwd()
     adj()
     fms, _ = timed(stream, fwd)
     ams, _ = timed(stream, adj)
+    pms, _ = timed(stream, lambda: adj(1))   # once more with every launch timed, for the roofline
     st = fitgb.fit_last_stats(g)
     fitgb.fit_grid_destroy(g)
     out = {"workload": "adjoint128", "cells": w.ncells, "nsteps": w.nsteps, "checkpoint_every": 100,
@@ -559,8 +561,10 @@ def adjoint_section(fitgb, dev, stream, peak):
     if st["step_ms"] > 0:
         achieved = st["alg_bytes"] / (st["step_ms"] / 1e3) / 1e9
         out["roofline"] = {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                           "share_of_time": st["step_ms"] / ams,
-                           "kernel": "step and gradient launches of the three sweeps"}
+                           "share_of_time": st["step_ms"] / pms, "launches": st["kernel_launches"],
+                           "alg_bytes": st["alg_bytes"],
+                           "kernel": "step and gradient launches of the three sweeps (forward, recompute, adjoint "
+                                     "with the gradient accumulation fused in)"}
     return out
 
 

@@ -106,9 +106,10 @@ typedef struct {
     int profile;                /* 1: time every step launch with CUDA events
                                    on the run's stream (fit_last_stats) [0]   */
     int kernel;                 /* step kernel: 1 shared-memory staging by
-                                   plain loads, 2 TMA pipeline; precision 40:
-                                   2 two cells per thread, 3 one cell per
-                                   thread [0 = 2]                             */
+                                   plain loads, 2 TMA pipeline (FP32 and
+                                   precision 40: two cells per thread), 3 the
+                                   TMA pipeline with one cell per thread
+                                   [0 = 2]                                    */
     int stages;                 /* TMA ring depth in planes, 3 or 4 (FP32
                                    TMA kernels; 0 = the tile's default)       */
     int debug_wait_limit;       /* test hook: polls before a TMA-kernel wait

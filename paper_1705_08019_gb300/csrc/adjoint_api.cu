@@ -113,12 +113,45 @@ int adjoint_impl(fit_grid *g, double dt, long long N, const fit_source *src, int
     a.ch = (const T *)g->ch.p;
     a.nmem = 1;
     a.err = (int *)g->err.p;
+    // FP32 TMA runs fuse the gradient accumulation into the adjoint step
+    const bool fused = fp32_blocks && tile.kernel == 2 && step_grad_supported(tile);
+    // opts->profile: every step and gradient launch timed by CUDA events on the stream
+    // (stats.step_ms) with its algorithmic bytes (stats.alg_bytes)
+    const bool profile = opts && opts->profile;
+    long long nev = 0;
+    const double ncell_d = (double)g->ncell;
+    const double step_bytes = (12.0 * sizeof(T) + ((g->lossy ? 6.0 : 3.0) + (g->mu_array ? 3.0 : 0.0)) * sizeof(T)) *
+                              ncell_d;   // e, h in and out, coefficients once
+    auto timed = [&](double bytes, auto &&fn) -> cudaError_t {
+        if (profile) {
+            while ((long long)g->ev.size() < 2 * (nev + 1)) {
+                cudaEvent_t e;
+                cudaError_t ce = cudaEventCreate(&e);
+                if (ce != cudaSuccess) return ce;
+                g->ev.push_back(e);
+            }
+            cudaError_t ce = cudaEventRecord(g->ev[2 * nev], s);
+            if (ce != cudaSuccess) return ce;
+        }
+        cudaError_t ce = fn();
+        if (ce != cudaSuccess) return ce;
+        if (profile) {
+            if ((ce = cudaEventRecord(g->ev[2 * nev + 1], s)) != cudaSuccess) return ce;
+            ++nev;
+        }
+        g->stats.alg_bytes += bytes;
+        return cudaSuccess;
+    };
     auto step = [&](const TmaMaps &maps) -> cudaError_t {
         g->stats.step_launches += 1;
         g->stats.kernel_launches += 1;
         g->stats.cell_updates += g->ncell;
-        if (tile.kernel == 2) return launch_step_tma<T>(a, maps, tile, g->lossy, g->mu_array, false, s);
-        return launch_step<T>(a, tile, g->lossy, g->mu_array, false, s);
+        // the fused gradient adds e^{n+1}, e^n (read) and the FP32 block sum (read and write)
+        const double bytes = step_bytes + (a.gb ? 12.0 * sizeof(float) * ncell_d : 0.0);
+        return timed(bytes, [&]() {
+            if (tile.kernel == 2) return launch_step_tma<T>(a, maps, tile, g->lossy, g->mu_array, false, s);
+            return launch_step<T>(a, tile, g->lossy, g->mu_array, false, s);
+        });
     };
     auto set_forward_sources = [&]() {
         a.nsrc = nsrc;
@@ -188,19 +221,33 @@ int adjoint_impl(fit_grid *g, double dt, long long N, const fit_source *src, int
             const long long t = N - 1 - n;
             a.it = (int)t;
             a.parity = (int)(t & 1);
+            const T *e1 = ring + (size_t)(n + 1 - A) * n6, *e0 = ring + (size_t)(n - A) * n6;
+            if (fused) {   // gb += K mu^{n+1} (e^{n+1} - e^n) inside the adjoint step
+                a.ge1 = e1;
+                a.ge0 = e0;
+                a.gb = (float *)g->gblk.p;
+                for (int q = 0; q < 3; ++q) a.gk[q] = (float)K[q];
+            }
             FIT_CHECK(step(lam_maps));
+            a.gb = nullptr;
             const T *mu_in = lam + (size_t)(t & 1) * n6;
             if (fp32_blocks) {
-                FIT_CHECK(grad_accumulate_block(ncp, (const float *)mu_in, (const float *)(ring + (size_t)(n + 1 - A) * n6),
-                                                (const float *)(ring + (size_t)(n - A) * n6), K, (float *)g->gblk.p, s));
-                g->stats.kernel_launches += 1;
+                if (!fused) {
+                    FIT_CHECK(timed(15.0 * sizeof(float) * (double)ncp, [&]() {
+                        return grad_accumulate_block(ncp, (const float *)mu_in, (const float *)e1, (const float *)e0, K,
+                                                     (float *)g->gblk.p, s);
+                    }));
+                    g->stats.kernel_launches += 1;
+                }
                 if ((t + 1) % kGradBlock == 0 || t == N - 1) {
-                    FIT_CHECK(grad_flush(ncp, (float *)g->gblk.p, gacc, s));
+                    FIT_CHECK(timed(18.0 * sizeof(float) * (double)ncp,
+                                    [&]() { return grad_flush(ncp, (float *)g->gblk.p, gacc, s); }));
                     g->stats.kernel_launches += 1;
                 }
             } else {
-                FIT_CHECK(grad_accumulate<T>(ncp, mu_in, ring + (size_t)(n + 1 - A) * n6, ring + (size_t)(n - A) * n6,
-                                             K, gacc, s));
+                FIT_CHECK(timed(3.0 * (3.0 * sizeof(T) + 2.0 * sizeof(double)) * (double)ncp, [&]() {
+                    return grad_accumulate<T>(ncp, mu_in, e1, e0, K, gacc, s);
+                }));
                 g->stats.kernel_launches += 1;
             }
         }
@@ -218,6 +265,16 @@ int adjoint_impl(fit_grid *g, double dt, long long N, const fit_source *src, int
     if (grad_host)
         FIT_CHECK(cudaMemcpyAsync(grad_out, gout, sizeof(double) * (size_t)g->ncell, cudaMemcpyDeviceToHost, s));
     if (J_out) FIT_CHECK(cudaMemcpyAsync(J_out, Jdev, sizeof(double), kind_from_dev(J_out), s));
+    if (profile && nev > 0) {
+        FIT_CHECK(cudaStreamSynchronize(s));
+        double ms = 0.0;
+        for (long long q = 0; q < nev; ++q) {
+            float t = 0.f;
+            FIT_CHECK(cudaEventElapsedTime(&t, g->ev[2 * q], g->ev[2 * q + 1]));
+            ms += t;
+        }
+        g->stats.step_ms = ms;
+    }
     const bool host_out = grad_host || (J_out && !is_device(J_out));
     return finish(g, s, host_out);
 }

@@ -210,6 +210,8 @@ int batched_group(const std::vector<const fit_paraexp_problem *> &probs, bool lo
     }
     if (opts && opts->tile_z > 0) tile.kz = opts->tile_z;
     if (opts && (opts->stages == 3 || opts->stages == 4)) tile.stages = opts->stages;
+    const bool single = opts && opts->kernel == 3;   // one cell per thread instead of two
+    tile.single = single;
     int nsm = 152;
     {
         int dev = 0;
@@ -270,7 +272,7 @@ int batched_group(const std::vector<const fit_paraexp_problem *> &probs, bool lo
 
     // autotune: time a few iterations of each candidate, once per batch signature
     if (opts && opts->autotune && !(opts->tile_x > 0)) {
-        std::string sig = std::string("fp32") + (lossy ? "L" : "N");
+        std::string sig = std::string(single ? "fp32s" : "fp32") + (lossy ? "L" : "N");
         for (int gi = 0; gi < ng; ++gi) {
             const fit_grid *g = H[gi].p->grid;
             sig += ":" + std::to_string(g->nx) + "x" + std::to_string(g->ny) + "x" + std::to_string(g->nz) + "k" +
@@ -285,6 +287,7 @@ int batched_group(const std::vector<const fit_paraexp_problem *> &probs, bool lo
                 tile = f->second;
                 hit = true;
             } else if (tune_disk_lookup(key, &tile)) {
+                tile.single = single;
                 g_tune_cache[key] = tile;
                 hit = true;
             }
@@ -299,7 +302,8 @@ int batched_group(const std::vector<const fit_paraexp_problem *> &probs, bool lo
             cudaEvent_t e0, e1;
             FIT_CHECK(cudaEventCreate(&e0));
             FIT_CHECK(cudaEventCreate(&e1));
-            for (const Tile &c : cands) {
+            for (Tile c : cands) {
+                c.single = single;
                 if ((rc = upload(c))) continue;
                 const int ctas = batched_ctas_per_sm_f32(c, lossy) * nsm;
                 FIT_CHECK(cudaMemsetAsync(d_counter.p, 0, sizeof(int) * (size_t)std::max<long long>(nit_max, 8), s));

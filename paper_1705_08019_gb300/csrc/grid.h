@@ -198,6 +198,10 @@ inline Tile pick_tile(const fit_grid *g, const fit_run_opts *o) {
     // FP32 default: 64 x 4 tiles, a 3-plane ring (4 CTAs per SM), 64-plane chunks
     if ((g->prec == 32 || g->prec == 40) && !g->tile_fixed) t = Tile{64, 4, 64, 2, 3};
     if (o && o->kernel > 0) t.kernel = o->kernel;
+    if (t.kernel == 3) {   // the TMA pipeline with one cell per thread
+        t.kernel = 2;
+        t.single = true;
+    }
     if (o && o->tile_x > 0 && o->tile_y > 0) {
         t.tx = o->tile_x;
         t.ty = o->tile_y;
@@ -208,7 +212,7 @@ inline Tile pick_tile(const fit_grid *g, const fit_run_opts *o) {
         t.kernel = 2;
     } else if (g->prec == 40) {
         if (!res_tile_supported(t.tx, t.ty)) t.tx = 64, t.ty = 4;
-        t.kernel = (o && o->kernel == 3) ? 3 : 2;
+        t.kernel = 2;
     } else if (t.kernel == 2 && !tma_tile_supported(t.tx, t.ty, g->prec == 64 ? 8 : 4)) {
         t.kernel = 1;
     }

@@ -82,6 +82,12 @@ struct StepArgs {
     int *err;
     int wait_limit;   // polls before an mbarrier wait gives up (0: default)
     int extra_tx;     // test hook: bytes announced beyond a tile's first plane
+    // adjoint gradient fused into the step (FP32 TMA kernel; gb null = off):
+    // gb_a += gk_a * (mu_a * (e1_a - e0_a)) on every edge of the grid, mu the
+    // step's input e (the adjoint state), e1/e0 3 pitched components each
+    const T *ge1, *ge0;
+    float *gb;
+    float gk[3];
 };
 
 // One grid of a batched launch (device table).
@@ -121,6 +127,7 @@ struct Tile {
     int tx, ty, kz;
     int kernel;      // 1: shared-memory staging by plain loads, 2: TMA pipeline
     int stages = 0;  // TMA ring depth (0: the tile's default)
+    bool single = false;   // FP32 TMA kernels: one cell per thread instead of two
 };
 
 // step.cu: plain-load staging kernel
@@ -138,6 +145,8 @@ template <typename T>
 cudaError_t launch_step_tma(const StepArgs<T> &a, const TmaMaps &maps, Tile tile, bool lossy, bool mu_array,
                             bool energy, cudaStream_t s);
 bool tma_tile_supported(int tx, int ty, int elem_bytes);
+// tiles of the FP32 TMA step kernel with the fused adjoint gradient (StepArgs::gb)
+bool step_grad_supported(Tile tile);
 // batched persistent kernel (FP32): launch over b.nitems items with `ctas` CTAs
 cudaError_t launch_batched_f32(const BatchArgs<float> &b, Tile tile, bool lossy, int ctas, cudaStream_t s);
 int batched_ctas_per_sm_f32(Tile tile, bool lossy);

@@ -851,8 +851,8 @@ bool res_tile_supported(int tx, int ty) { return (tx == 32 && (ty == 4 || ty == 
 
 cudaError_t launch_step_res(const StepArgs<float> &a, const TmaMaps &maps, Tile t, bool lossy, bool muarr,
                             bool energy, cudaStream_t s) {
-    // two cells per thread unless kernel 3 (one cell per thread) is asked for
-    if (t.kernel != 3) {
+    // two cells per thread unless one cell per thread (opts kernel 3) is asked for
+    if (!t.single) {
 #define FIT_R2(TX, TY, S)                                                               \
         if (t.tx == TX && t.ty == TY)                                                   \
             return lossy ? res::launch2<TX, TY, S, true>(a, maps, muarr, energy, s)     \

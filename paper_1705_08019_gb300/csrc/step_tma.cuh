@@ -157,6 +157,9 @@ struct TileJob {
     int *err;
     int wait_limit;           // polls per wait (kWaitLimit when 0)
     int extra_tx;             // test hook, see StepArgs
+    const T *ge1, *ge0;       // fused adjoint gradient (GRAD kernels), see StepArgs
+    float *gb;
+    float gk[3];
 };
 
 // Shared memory of the tile pipeline (dynamic stage ring + these statics).
@@ -173,7 +176,7 @@ struct TileSmem {
 // One tile column of one step.  `phase` holds the parity of each stage's
 // mbarrier; it carries over between calls on the same CTA.  Returns false if
 // a bounded wait gave up (kErrTimeout recorded, no copy left in flight).
-template <typename T, int TX, int TY, int S, bool LOSSY>
+template <typename T, int TX, int TY, int S, bool LOSSY, bool GRAD = false>
 __device__ __forceinline__ bool tma_tile(const TileJob<T> &J, const CUtensorMap *tm_state,
                                          const CUtensorMap *tm_coef, unsigned char *dsm,
                                          TileSmem<T, TX, TY, S> &sm, uint32_t &phase) {
@@ -365,6 +368,11 @@ __device__ __forceinline__ bool tma_tile(const TileJob<T> &J, const CUtensorMap 
             out[c] = exn;
             out[ncell + c] = eyn;
             out[2 * ncell + c] = ezn;
+            if (GRAD) {   // the input e is the adjoint state mu^{n+1}
+                J.gb[c] += J.gk[0] * (ex0 * (J.ge1[c] - J.ge0[c]));
+                J.gb[ncell + c] += J.gk[1] * (ey0 * (J.ge1[ncell + c] - J.ge0[ncell + c]));
+                J.gb[2 * ncell + c] += J.gk[2] * (ez0 * (J.ge1[2 * ncell + c] - J.ge0[2 * ncell + c]));
+            }
             for (int q = 0; q < sm.nprb; ++q) {
                 const EdgeRef r = sm.prb_ref[q];
                 if (r.i == i && r.j == j && r.k == k) {
@@ -429,7 +437,7 @@ __device__ __forceinline__ unsigned char *aligned_dsm() {
 }
 
 // Single grid: one CTA = one (member, tile, chunk), member fastest.
-template <typename T, int TX, int TY, int S, bool LOSSY>
+template <typename T, int TX, int TY, int S, bool LOSSY, bool GRAD = false>
 __global__ void __launch_bounds__(TX *TY) step_tma_kernel(const __grid_constant__ StepArgs<T> a,
                                                           const __grid_constant__ CUtensorMap tm_state,
                                                           const __grid_constant__ CUtensorMap tm_coef, int muarr,
@@ -461,13 +469,19 @@ __global__ void __launch_bounds__(TX *TY) step_tma_kernel(const __grid_constant_
     J.err = a.err;
     J.wait_limit = a.wait_limit;
     J.extra_tx = a.extra_tx;
+    J.ge1 = a.ge1;
+    J.ge0 = a.ge0;
+    J.gb = a.gb;
+    J.gk[0] = a.gk[0];
+    J.gk[1] = a.gk[1];
+    J.gk[2] = a.gk[2];
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) mbar_init(&sm.bar[s], 1);
         mbar_init_fence();
     }
     __syncthreads();
     uint32_t phase = 0;
-    tma_tile<T, TX, TY, S, LOSSY>(J, &tm_state, &tm_coef, dsm, sm, phase);
+    tma_tile<T, TX, TY, S, LOSSY, GRAD>(J, &tm_state, &tm_coef, dsm, sm, phase);
 }
 
 // Many grids: persistent CTAs (about one per resident slot) take work items
@@ -520,12 +534,12 @@ __global__ void __launch_bounds__(TX *TY) batched_tma_kernel(const __grid_consta
     }
 }
 
-template <typename T, int TX, int TY, int S, bool LOSSY>
+template <typename T, int TX, int TY, int S, bool LOSSY, bool GRAD = false>
 cudaError_t launch_one(const StepArgs<T> &a, const TmaMaps &maps, bool muarr, bool energy, cudaStream_t s) {
     using G = Geometry<T, TX, TY, S, LOSSY>;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(step_tma_kernel<T, TX, TY, S, LOSSY>,
+        cudaError_t e = cudaFuncSetAttribute(step_tma_kernel<T, TX, TY, S, LOSSY, GRAD>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, G::DYN_SMEM);
         if (e != cudaSuccess) return e;
         attr_set = true;
@@ -533,7 +547,7 @@ cudaError_t launch_one(const StepArgs<T> &a, const TmaMaps &maps, bool muarr, bo
     const long long blocks = (long long)a.nmem * a.tiles_x * a.tiles_y * a.nchunk;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    step_tma_kernel<T, TX, TY, S, LOSSY><<<(unsigned)blocks, TX * TY, G::DYN_SMEM, s>>>(
+    step_tma_kernel<T, TX, TY, S, LOSSY, GRAD><<<(unsigned)blocks, TX * TY, G::DYN_SMEM, s>>>(
         a, maps.state, maps.coef, muarr ? 1 : 0, energy ? 1 : 0);
     return cudaGetLastError();
 }

@@ -2,7 +2,7 @@
 // tensor-map encoder.
 #include <cudaTypedefs.h>
 
-#include "step_tma.cuh"
+#include "step_tma2.cuh"
 
 namespace fitgb {
 
@@ -11,10 +11,51 @@ bool tma_tile_supported(int tx, int ty, int elem_bytes) {
     return (tx == 32 && (ty == 4 || ty == 8 || ty == 16)) || (tx == 64 && ty == 4);
 }
 
+bool step_grad_supported(Tile t) {
+    if (!t.single) return (t.tx == 64 && t.ty == 4) || (t.tx == 32 && t.ty == 8);
+    return (t.tx == 64 && t.ty == 4 && (t.stages == 0 || t.stages == 3)) ||
+           (t.tx == 32 && t.ty == 8 && (t.stages == 0 || t.stages == 4));
+}
+
+// Tiles of the two-cells-per-thread kernels and their ring depths (the first
+// listed for a tile is its default): (64, 4) 3 or 4, (32, 8) 4 or 3,
+// (32, 16) 3, (32, 4) 4.
 template <>
 cudaError_t launch_step_tma<float>(const StepArgs<float> &a, const TmaMaps &maps, Tile t, bool lossy, bool muarr,
                                    bool energy, cudaStream_t s) {
     using namespace tma;
+    if (!t.single) {
+        if (a.gb) {   // the adjoint step with the gradient accumulation fused in
+            if (t.tx == 64 && t.ty == 4)
+                return lossy ? launch_two<64, 4, 3, true, true>(a, maps, muarr, energy, s)
+                             : launch_two<64, 4, 3, false, true>(a, maps, muarr, energy, s);
+            if (t.tx == 32 && t.ty == 8)
+                return lossy ? launch_two<32, 8, 4, true, true>(a, maps, muarr, energy, s)
+                             : launch_two<32, 8, 4, false, true>(a, maps, muarr, energy, s);
+            return cudaErrorInvalidValue;
+        }
+#define FIT_T2(TX, TY, S)                                                                  \
+        if (t.tx == TX && t.ty == TY && (t.stages == 0 || t.stages == S))                  \
+            return lossy ? launch_two<TX, TY, S, true>(a, maps, muarr, energy, s)          \
+                         : launch_two<TX, TY, S, false>(a, maps, muarr, energy, s);
+        FIT_T2(64, 4, 3)
+        FIT_T2(64, 4, 4)
+        FIT_T2(32, 8, 4)
+        FIT_T2(32, 8, 3)
+        FIT_T2(32, 16, 3)
+        FIT_T2(32, 4, 4)
+#undef FIT_T2
+        return cudaErrorInvalidValue;
+    }
+    if (a.gb) {   // the adjoint step with the gradient accumulation fused in
+        if (t.tx == 64 && t.ty == 4 && (t.stages == 0 || t.stages == 3))
+            return lossy ? launch_one<float, 64, 4, 3, true, true>(a, maps, muarr, energy, s)
+                         : launch_one<float, 64, 4, 3, false, true>(a, maps, muarr, energy, s);
+        if (t.tx == 32 && t.ty == 8 && (t.stages == 0 || t.stages == 4))
+            return lossy ? launch_one<float, 32, 8, 4, true, true>(a, maps, muarr, energy, s)
+                         : launch_one<float, 32, 8, 4, false, true>(a, maps, muarr, energy, s);
+        return cudaErrorInvalidValue;
+    }
     if (t.stages != 0 && !((t.tx == 32 && t.ty == 8) || (t.tx == 64 && t.ty == 4)))
         t.stages = 0;   // a ring depth this tile has no variant for: its default
 #define FIT_T(TX, TY, S)                                                                   \
@@ -37,6 +78,20 @@ bool batched_tile_supported(int tx, int ty) {
 
 cudaError_t launch_batched_f32(const BatchArgs<float> &b, Tile t, bool lossy, int ctas, cudaStream_t s) {
     using namespace tma;
+    if (!t.single) {
+#define FIT_T2(TX, TY, S)                                                                         \
+        if (t.tx == TX && t.ty == TY && (t.stages == 0 || t.stages == S))                         \
+            return lossy ? launch_batched_two<TX, TY, S, true>(b, ctas, s)                        \
+                         : launch_batched_two<TX, TY, S, false>(b, ctas, s);
+        FIT_T2(32, 8, 4)
+        FIT_T2(32, 8, 3)
+        FIT_T2(32, 16, 3)
+        FIT_T2(32, 4, 4)
+        FIT_T2(64, 4, 3)
+        FIT_T2(64, 4, 4)
+#undef FIT_T2
+        return cudaErrorInvalidValue;
+    }
     if (t.stages != 0 && !((t.tx == 32 && t.ty == 8) || (t.tx == 64 && t.ty == 4))) t.stages = 0;
 #define FIT_T(TX, TY, S)                                                                          \
     if (t.tx == TX && t.ty == TY && (t.stages == 0 || t.stages == S))                             \
@@ -54,6 +109,19 @@ cudaError_t launch_batched_f32(const BatchArgs<float> &b, Tile t, bool lossy, in
 
 int batched_ctas_per_sm_f32(Tile t, bool lossy) {
     using namespace tma;
+    if (!t.single) {
+#define FIT_T2(TX, TY, S)                                                                         \
+        if (t.tx == TX && t.ty == TY && (t.stages == 0 || t.stages == S))                         \
+            return lossy ? batched_two_occupancy<TX, TY, S, true>() : batched_two_occupancy<TX, TY, S, false>();
+        FIT_T2(32, 8, 4)
+        FIT_T2(32, 8, 3)
+        FIT_T2(32, 16, 3)
+        FIT_T2(32, 4, 4)
+        FIT_T2(64, 4, 3)
+        FIT_T2(64, 4, 4)
+#undef FIT_T2
+        return 1;
+    }
     if (t.stages != 0 && !((t.tx == 32 && t.ty == 8) || (t.tx == 64 && t.ty == 4))) t.stages = 0;
 #define FIT_T(TX, TY, S)                                                                          \
     if (t.tx == TX && t.ty == TY && (t.stages == 0 || t.stages == S))                             \
