@@ -223,7 +223,7 @@ class Clocks:
 
 
 # ncu summary of each precision's step kernel: (profile, kernel source, hash key)
-PROFILES = {32: ("step_tma_kernel_boxes256.md", "step_tma.cuh", "step_tma_cuh_sha256"),
+PROFILES = {32: ("step_tma2_kernel_boxes256.md", "step_tma2.cuh", "step_tma2_cuh_sha256"),
             40: ("step_res2_kernel_boxes256.md", "step_res.cu", "step_res_cu_sha256")}
 
 
@@ -598,8 +598,9 @@ def ncu_case(args):
     g = fitgb.fit_grid_create(w.dims, w.spacing, eps, None, sig, w.precision)
     dt = w.cfl_fraction * fitgb.fit_cfl_dt(g)
     s = torch.cuda.current_stream(dev)
+    ko = fitgb.make_opts(kernel=args.kernel)   # the step kernel variant (--kernel)
     if args.ncu_case == "leapfrog":
-        fitgb.fit_leapfrog_run(g, dt, args.ncu_steps, 0, w.sources, w.probes, None, None, None, None, None, s)
+        fitgb.fit_leapfrog_run(g, dt, args.ncu_steps, 0, w.sources, w.probes, None, None, None, None, ko, s)
     elif args.ncu_case == "expo":
         # one Leja substep of degree 8 over --ncu-steps steps from a seeded state
         from paper_1705_08019_gb300 import workloads as W
@@ -609,11 +610,11 @@ def ncu_case(args):
     elif args.ncu_case == "solve":
         # the workload's K equal windows over --ncu-steps steps: launches with the member counts of a full solve
         w.nsteps = args.ncu_steps
-        fitgb.paraexp_run(g, dt, w.K, w.windows(), w.sources, w.probes, None, None, None, None, None, None, s)
+        fitgb.paraexp_run(g, dt, w.K, w.windows(), w.sources, w.probes, None, None, None, None, None, ko, s)
     else:
         K = args.ncu_members
         win = np.array([j for j in range(K)] + [args.ncu_steps], dtype=np.int64)
-        fitgb.paraexp_run(g, dt, K, win, w.sources, w.probes, None, None, None, None, None, None, s)
+        fitgb.paraexp_run(g, dt, K, win, w.sources, w.probes, None, None, None, None, None, ko, s)
     torch.cuda.synchronize()
     fitgb.fit_grid_destroy(g)
 
