@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(TX *TY, 3) step_res_kernel(const __grid_consta
 // and B = A + u_x, so shared-memory and global accesses are 8 bytes wide, B's
 // low-x neighbour is A itself and A's high-x neighbour is B.  The low-y halo
 // row is computed by the first TX/2 threads (pairs), the low-x halo column by
-// the next TY threads (single cells).
+// the last TY threads (single cells).
 template <int TX, int TY, int S, bool LOSSY>
 __global__ void __launch_bounds__(TX / 2 * TY, 3) step_res2_kernel(const __grid_constant__ StepArgs<float> a,
                                                                const __grid_constant__ CUtensorMap tm_state,
@@ -526,7 +526,9 @@ __global__ void __launch_bounds__(TX / 2 * TY, 3) step_res2_kernel(const __grid_
         ch2 = a.ch[2];
     }
     const bool hy_row = tid < PX;                   // low-y halo row, pair tid
-    const bool hx_col = tid >= PX && tid < PX + TY; // low-x halo column, cell tid - PX
+    // low-x halo column: the last TY threads, cell tid - (NT - TY) (another warp than the
+    // halo row's whenever the tile has more than one warp, so no warp runs both branches)
+    const bool hx_col = tid >= NT - TY;
     float2 hxp = make_float2(0.f, 0.f), hyp = hxp, hxpl = hxp, hypl = hxp;   // h_x, h_y of plane k-1
     double wsum = 0.0;
     uint32_t phase = 0;
@@ -649,7 +651,7 @@ __global__ void __launch_bounds__(TX / 2 * TY, 3) step_res2_kernel(const __grid_
                 *reinterpret_cast<float2 *>(&sHh[2][0][2 * t + 2]) = h2;
                 *reinterpret_cast<float2 *>(&sHl[2][0][2 * t + 2]) = h2l;
             } else if (hx_col) {   // cell (i0-1, j0+y-1): window x = 3; h_y and h_z
-                const int y = tid - PX + 1;
+                const int y = tid - (NT - TY) + 1;
                 float c1 = ch1, c2 = ch2;
                 if (muarr) {
                     const int hi = i0 - 1, hj = j0 + y - 1;

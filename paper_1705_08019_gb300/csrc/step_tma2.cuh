@@ -12,7 +12,7 @@
 //     the source and probe checks) is paid once per two cells.
 // The arithmetic of each cell is the same expression, in the same order, as in
 // tma_tile, so both kernels give the same fields.  The first TX/2 threads also
-// compute the low-y halo row (pairs), the next TY threads the low-x halo
+// compute the low-y halo row (pairs), the last TY threads the low-x halo
 // column (single cells).
 #pragma once
 
@@ -114,7 +114,9 @@ __device__ __forceinline__ bool tma_tile2(const TileJob<float> &J, const CUtenso
         mu2 = J.mmu[2];
     }
     const bool hy_row = tid < PX;                   // low-y halo row, pair tid
-    const bool hx_col = tid >= PX && tid < PX + TY; // low-x halo column, cell tid - PX
+    // low-x halo column: the last TY threads, cell tid - (NT - TY) (another warp than the
+    // halo row's whenever the tile has more than one warp, so no warp runs both branches)
+    const bool hx_col = tid >= NT - TY;
     float2 hxp = make_float2(0.f, 0.f), hyp = hxp;  // h_x, h_y at (., j, k-1), step n+1/2
     Acc<float> wacc;
     int bad = wait_plane(0) ? 0 : 1;
@@ -181,7 +183,7 @@ __device__ __forceinline__ bool tma_tile2(const TileJob<float> &J, const CUtenso
                 *reinterpret_cast<float2 *>(&sm.sH[2][0][2 * t + 2]) =
                     make_float2(h2.x - c2.x * cza, h2.y - c2.y * czb);
             } else if (hx_col) {   // cell (i0-1, j0+y-1): window x = 3; h_y and h_z
-                const int y = tid - PX + 1;
+                const int y = tid - (NT - TY) + 1;
                 float c1 = ch1, c2 = ch2;
                 if (J.muarr) {
                     const int hi = i0 - 1, hj = j0 + y - 1;
