@@ -134,6 +134,11 @@ typedef struct {
                                    steps per launch (temporal blocking: the
                                    fields are read and written once per two
                                    steps), 1 one step [0 = 1]                 */
+    int adjoint_mem_mb;         /* fit_adjoint_grad on FP32 grids: device
+                                   memory (MiB) it may use to keep the forward
+                                   sweep's e^{n+1} - e^n of its last checkpoint
+                                   segments, which then need no recompute
+                                   (3 floats per cell and kept step) [0]      */
 } fit_run_opts;
 
 /* Propagators of the homogeneous problems w_j (opts->homogeneous). */

@@ -115,6 +115,21 @@ int adjoint_impl(fit_grid *g, double dt, long long N, const fit_source *src, int
     a.err = (int *)g->err.p;
     // FP32 TMA runs fuse the gradient accumulation into the adjoint step
     const bool fused = fp32_blocks && tile.kernel == 2 && step_grad_supported(tile);
+    // With a memory budget (opts->adjoint_mem_mb, two-cell FP32 kernel) the forward sweep keeps
+    // d^n = e^{n+1} - e^n of its last segments; those segments skip the recompute, and their
+    // adjoint steps read d^n instead of two ring states.  The kernel forms d^n with the same
+    // float subtraction the adjoint step would, so the gradient is the same bits.
+    long long seg_keep0 = nseg;   // first segment whose differences are kept
+    if (fused && !tile.single && opts && opts->adjoint_mem_mb > 0) {
+        const double per_step = 3.0 * (double)ncp * sizeof(float);
+        const double budget = (double)opts->adjoint_mem_mb * 1048576.0;
+        while (seg_keep0 > 0 && (double)(N - (seg_keep0 - 1) * C) * per_step <= budget) --seg_keep0;
+        if (seg_keep0 < nseg &&
+            ensure(g->dhist, (size_t)(N - seg_keep0 * C) * 3 * (size_t)ncp * sizeof(float)) != FIT_OK)
+            seg_keep0 = nseg;   // no room after all: recompute every segment
+    }
+    const long long A_keep = seg_keep0 * C;   // steps n >= A_keep keep d^n
+    float *dhist = (float *)g->dhist.p;
     // opts->profile: every step and gradient launch timed by CUDA events on the stream
     // (stats.step_ms) with its algorithmic bytes (stats.alg_bytes)
     const bool profile = opts && opts->profile;
@@ -146,8 +161,10 @@ int adjoint_impl(fit_grid *g, double dt, long long N, const fit_source *src, int
         g->stats.step_launches += 1;
         g->stats.kernel_launches += 1;
         g->stats.cell_updates += g->ncell;
-        // the fused gradient adds e^{n+1}, e^n (read) and the FP32 block sum (read and write)
-        const double bytes = step_bytes + (a.gb ? 12.0 * sizeof(float) * ncell_d : 0.0);
+        // the fused gradient adds e^{n+1}, e^n (or d^n) read and the FP32 block sum read and
+        // written; keeping d^n adds its write
+        const double bytes = step_bytes + (a.gb ? (a.ge0 ? 12.0 : 9.0) * sizeof(float) * ncell_d : 0.0) +
+                             (a.gd ? 3.0 * sizeof(float) * ncell_d : 0.0);
         return timed(bytes, [&]() {
             if (tile.kernel == 2) return launch_step_tma<T>(a, maps, tile, g->lossy, g->mu_array, false, s);
             return launch_step<T>(a, tile, g->lossy, g->mu_array, false, s);
@@ -167,13 +184,15 @@ int adjoint_impl(fit_grid *g, double dt, long long N, const fit_source *src, int
     for (int q = 0; q < nprb; ++q) a.prb[q] = {prb[q].axis, prb[q].i, prb[q].j, prb[q].k};
     a.mem = mdev;
     for (long long n = 0; n < N; ++n) {
-        if (want_grad && n % C == 0)
+        if (want_grad && n % C == 0 && n < A_keep)
             FIT_CHECK(cudaMemcpyAsync(ckpt + (size_t)(n / C) * n6, ring + (size_t)(n & 1) * n6, n6 * sizeof(T),
                                       cudaMemcpyDeviceToDevice, s));
         a.it = (int)n;
         a.parity = (int)(n & 1);
+        a.gd = (want_grad && n >= A_keep) ? dhist + (size_t)(n - A_keep) * 3 * (size_t)ncp : nullptr;
         FIT_CHECK(step(ring_maps));
     }
+    a.gd = nullptr;
     a.nprb = 0;
     // each probe edge's length: the grid step, or on a graded grid the size of
     // the cell the edge runs through along its axis
@@ -202,9 +221,11 @@ int adjoint_impl(fit_grid *g, double dt, long long N, const fit_source *src, int
 
     for (long long sg = nseg - 1; sg >= 0; --sg) {
         const long long A = sg * C, B = std::min<long long>(A + C, N);
-        FIT_CHECK(cudaMemcpyAsync(ring, ckpt + (size_t)sg * n6, n6 * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        const bool kept = sg >= seg_keep0;   // d^n of this segment came from the forward sweep
+        if (!kept)
+            FIT_CHECK(cudaMemcpyAsync(ring, ckpt + (size_t)sg * n6, n6 * sizeof(T), cudaMemcpyDeviceToDevice, s));
         set_forward_sources();
-        for (long long q = 0; q < B - A; ++q) {   // ring slot q -> q+1: step A+q
+        for (long long q = 0; !kept && q < B - A; ++q) {   // ring slot q -> q+1: step A+q
             a.mem = mdev + 1 + q;
             a.it = (int)A;
             a.parity = 0;
@@ -223,8 +244,8 @@ int adjoint_impl(fit_grid *g, double dt, long long N, const fit_source *src, int
             a.parity = (int)(t & 1);
             const T *e1 = ring + (size_t)(n + 1 - A) * n6, *e0 = ring + (size_t)(n - A) * n6;
             if (fused) {   // gb += K mu^{n+1} (e^{n+1} - e^n) inside the adjoint step
-                a.ge1 = e1;
-                a.ge0 = e0;
+                a.ge1 = kept ? (const T *)(dhist + (size_t)(n - A_keep) * 3 * (size_t)ncp) : e1;
+                a.ge0 = kept ? nullptr : e0;
                 a.gb = (float *)g->gblk.p;
                 for (int q = 0; q < 3; ++q) a.gk[q] = (float)K[q];
             }

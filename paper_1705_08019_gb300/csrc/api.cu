@@ -644,7 +644,7 @@ void fit_grid_destroy(fit_grid *g) {
     Buf *bufs[] = {&g->coef, &g->ch, &g->meps, &g->mmu, &g->state, &g->pm, &g->amp, &g->srcdev,
                    &g->memdev, &g->acc, &g->kahan, &g->stage, &g->energy, &g->scratch, &g->probe_ws, &g->err,
                    &g->ckpt, &g->ring, &g->lam, &g->gacc, &g->aprobe, &g->aamp, &g->adjmem, &g->scalar,
-                   &g->grad_ws, &g->xblocks, &g->xtab, &g->xbasis, &g->xpm, &g->spc, &g->gblk};
+                   &g->grad_ws, &g->xblocks, &g->xtab, &g->xbasis, &g->xpm, &g->spc, &g->gblk, &g->dhist};
     for (Buf *b : bufs) release(*b);
     for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
     delete g;

@@ -43,7 +43,7 @@ struct fit_grid {
     Buf coef, ch, meps, mmu;   // coef: cb (3 components) then ca (3, lossy only)
     // workspaces
     Buf state, pm, amp, srcdev, memdev, acc, kahan, stage, energy, scratch, probe_ws, err;
-    Buf ckpt, ring, lam, gacc, gblk, aprobe, aamp, adjmem, scalar, grad_ws;   // adjoint workspaces
+    Buf ckpt, ring, lam, gacc, gblk, aprobe, aamp, adjmem, scalar, grad_ws, dhist;   // adjoint workspaces
     Buf xblocks, xtab, xbasis, xpm;   // exponential propagators: state blocks, tables, probe basis, probe rows
     int deferred = 0;
     fitgb::Tile tile = {32, 8, 32, 2};

@@ -88,6 +88,9 @@ struct StepArgs {
     const T *ge1, *ge0;
     float *gb;
     float gk[3];
+    // forward sweep keeping e^{n+1} - e^n for the adjoint (FP32 two-cell TMA kernel; null = off):
+    // 3 pitched components; an adjoint step then takes them in ge1 with ge0 null
+    float *gd;
 };
 
 // One grid of a batched launch (device table).

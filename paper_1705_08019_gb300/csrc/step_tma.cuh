@@ -160,6 +160,7 @@ struct TileJob {
     const T *ge1, *ge0;       // fused adjoint gradient (GRAD kernels), see StepArgs
     float *gb;
     float gk[3];
+    float *gd;                // e^{n+1} - e^n output of the forward sweep (two-cell FP32 kernel), see StepArgs
 };
 
 // Shared memory of the tile pipeline (dynamic stage ring + these statics).

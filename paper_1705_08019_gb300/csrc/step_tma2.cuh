@@ -21,6 +21,11 @@
 namespace fitgb {
 namespace tma {
 
+// optional epilogues of the two-cell step kernel (template parameter EXTRA)
+constexpr int kExtraNone = 0;
+constexpr int kExtraGrad = 1;   // adjoint step: accumulate the gradient (StepArgs gb, ge1, ge0, gk)
+constexpr int kExtraDiff = 2;   // forward step: write e^{n+1} - e^n (StepArgs gd)
+
 template <int TX, int TY, int S>
 struct TileSmem2 {
     uint64_t bar[S];
@@ -35,7 +40,7 @@ struct TileSmem2 {
 
 // One tile column of one step with two cells per thread; see tma_tile for the
 // contract (phase, return value, error handling).
-template <int TX, int TY, int S, bool LOSSY, bool GRAD = false>
+template <int TX, int TY, int S, bool LOSSY, int EXTRA = 0>
 __device__ __forceinline__ bool tma_tile2(const TileJob<float> &J, const CUtensorMap *tm_state,
                                           const CUtensorMap *tm_coef, unsigned char *dsm,
                                           TileSmem2<TX, TY, S> &sm, uint32_t &phase) {
@@ -249,10 +254,18 @@ __device__ __forceinline__ bool tma_tile2(const TileJob<float> &J, const CUtenso
                 *reinterpret_cast<float2 *>(out + ncell + c) = eyn;
                 *reinterpret_cast<float2 *>(out + 2 * ncell + c) = ezn;
             }
-            if (GRAD) {   // the input e is the adjoint state mu^{n+1}
-                const float2 a1 = F2(J.ge1 + c), a0 = F2(J.ge0 + c);
-                const float2 b1 = F2(J.ge1 + ncell + c), b0 = F2(J.ge0 + ncell + c);
-                const float2 z1 = F2(J.ge1 + 2 * ncell + c), z0 = F2(J.ge0 + 2 * ncell + c);
+            if (EXTRA == kExtraDiff && !bad) {   // keep e^{n+1} - e^n for the adjoint's gradient
+                float *d = J.gd;
+                *reinterpret_cast<float2 *>(d + c) = make_float2(exn.x - ex.x, exn.y - ex.y);
+                *reinterpret_cast<float2 *>(d + ncell + c) = make_float2(eyn.x - ey.x, eyn.y - ey.y);
+                *reinterpret_cast<float2 *>(d + 2 * ncell + c) = make_float2(ezn.x - ez.x, ezn.y - ez.y);
+            }
+            if (EXTRA == kExtraGrad) {   // the input e is the adjoint state mu^{n+1}
+                // e^{n+1} - e^n from two states, or (ge0 null) kept by the forward sweep in ge1
+                const float2 zero = make_float2(0.f, 0.f);
+                const float2 a1 = F2(J.ge1 + c), a0 = J.ge0 ? F2(J.ge0 + c) : zero;
+                const float2 b1 = F2(J.ge1 + ncell + c), b0 = J.ge0 ? F2(J.ge0 + ncell + c) : zero;
+                const float2 z1 = F2(J.ge1 + 2 * ncell + c), z0 = J.ge0 ? F2(J.ge0 + 2 * ncell + c) : zero;
                 float2 *gx = reinterpret_cast<float2 *>(J.gb + c);
                 float2 *gy = reinterpret_cast<float2 *>(J.gb + ncell + c);
                 float2 *gz = reinterpret_cast<float2 *>(J.gb + 2 * ncell + c);
@@ -332,7 +345,7 @@ __device__ __forceinline__ bool tma_tile2(const TileJob<float> &J, const CUtenso
 }
 
 // Single grid, two cells per thread: one CTA = one (member, tile, chunk), member fastest.
-template <int TX, int TY, int S, bool LOSSY, bool GRAD = false>
+template <int TX, int TY, int S, bool LOSSY, int EXTRA = 0>
 __global__ void __launch_bounds__(TX / 2 * TY, 4) step_tma2_kernel(const __grid_constant__ StepArgs<float> a,
                                                                const __grid_constant__ CUtensorMap tm_state,
                                                                const __grid_constant__ CUtensorMap tm_coef,
@@ -370,18 +383,19 @@ __global__ void __launch_bounds__(TX / 2 * TY, 4) step_tma2_kernel(const __grid_
     J.gk[0] = a.gk[0];
     J.gk[1] = a.gk[1];
     J.gk[2] = a.gk[2];
+    J.gd = a.gd;
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) mbar_init(&sm.bar[s], 1);
         mbar_init_fence();
     }
     __syncthreads();
     uint32_t phase = 0;
-    tma_tile2<TX, TY, S, LOSSY, GRAD>(J, &tm_state, &tm_coef, dsm, sm, phase);
+    tma_tile2<TX, TY, S, LOSSY, EXTRA>(J, &tm_state, &tm_coef, dsm, sm, phase);
 }
 
 // Many grids, two cells per thread: the persistent work loop of batched_tma_kernel.
 template <int TX, int TY, int S, bool LOSSY>
-__global__ void __launch_bounds__(TX / 2 * TY, 4) batched_tma2_kernel(const __grid_constant__ BatchArgs<float> b) {
+__global__ void __launch_bounds__(TX / 2 * TY, (TX / 2 * TY == 128 && S == 3) ? 5 : 4) batched_tma2_kernel(const __grid_constant__ BatchArgs<float> b) {
     __shared__ TileSmem2<TX, TY, S> sm;
     unsigned char *dsm = aligned_dsm<float, TX, TY, S>();
     if (threadIdx.x == 0) {
@@ -423,16 +437,17 @@ __global__ void __launch_bounds__(TX / 2 * TY, 4) batched_tma2_kernel(const __gr
         J.ge1 = J.ge0 = nullptr;
         J.gb = nullptr;
         J.gk[0] = J.gk[1] = J.gk[2] = 0.f;
+        J.gd = nullptr;
         if (!tma_tile2<TX, TY, S, LOSSY>(J, &b.maps[2 * w.grid], &b.maps[2 * w.grid + 1], dsm, sm, phase)) return;
     }
 }
 
-template <int TX, int TY, int S, bool LOSSY, bool GRAD = false>
+template <int TX, int TY, int S, bool LOSSY, int EXTRA = 0>
 cudaError_t launch_two(const StepArgs<float> &a, const TmaMaps &maps, bool muarr, bool energy, cudaStream_t s) {
     using G = Geometry<float, TX, TY, S, LOSSY>;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(step_tma2_kernel<TX, TY, S, LOSSY, GRAD>,
+        cudaError_t e = cudaFuncSetAttribute(step_tma2_kernel<TX, TY, S, LOSSY, EXTRA>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, G::DYN_SMEM);
         if (e != cudaSuccess) return e;
         attr_set = true;
@@ -440,7 +455,7 @@ cudaError_t launch_two(const StepArgs<float> &a, const TmaMaps &maps, bool muarr
     const long long blocks = (long long)a.nmem * a.tiles_x * a.tiles_y * a.nchunk;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    step_tma2_kernel<TX, TY, S, LOSSY, GRAD><<<(unsigned)blocks, TX / 2 * TY, G::DYN_SMEM, s>>>(
+    step_tma2_kernel<TX, TY, S, LOSSY, EXTRA><<<(unsigned)blocks, TX / 2 * TY, G::DYN_SMEM, s>>>(
         a, maps.state, maps.coef, muarr ? 1 : 0, energy ? 1 : 0);
     return cudaGetLastError();
 }

@@ -25,13 +25,22 @@ cudaError_t launch_step_tma<float>(const StepArgs<float> &a, const TmaMaps &maps
                                    bool energy, cudaStream_t s) {
     using namespace tma;
     if (!t.single) {
-        if (a.gb) {   // the adjoint step with the gradient accumulation fused in
-            if (t.tx == 64 && t.ty == 4)
-                return lossy ? launch_two<64, 4, 3, true, true>(a, maps, muarr, energy, s)
-                             : launch_two<64, 4, 3, false, true>(a, maps, muarr, energy, s);
-            if (t.tx == 32 && t.ty == 8)
-                return lossy ? launch_two<32, 8, 4, true, true>(a, maps, muarr, energy, s)
-                             : launch_two<32, 8, 4, false, true>(a, maps, muarr, energy, s);
+        if (a.gb || a.gd) {   // the adjoint step with the gradient fused in, or a forward step keeping e^{n+1}-e^n
+            if (a.gb && a.gd) return cudaErrorInvalidValue;
+            if (t.tx == 64 && t.ty == 4) {
+                if (a.gd)
+                    return lossy ? launch_two<64, 4, 3, true, kExtraDiff>(a, maps, muarr, energy, s)
+                                 : launch_two<64, 4, 3, false, kExtraDiff>(a, maps, muarr, energy, s);
+                return lossy ? launch_two<64, 4, 3, true, kExtraGrad>(a, maps, muarr, energy, s)
+                             : launch_two<64, 4, 3, false, kExtraGrad>(a, maps, muarr, energy, s);
+            }
+            if (t.tx == 32 && t.ty == 8) {
+                if (a.gd)
+                    return lossy ? launch_two<32, 8, 4, true, kExtraDiff>(a, maps, muarr, energy, s)
+                                 : launch_two<32, 8, 4, false, kExtraDiff>(a, maps, muarr, energy, s);
+                return lossy ? launch_two<32, 8, 4, true, kExtraGrad>(a, maps, muarr, energy, s)
+                             : launch_two<32, 8, 4, false, kExtraGrad>(a, maps, muarr, energy, s);
+            }
             return cudaErrorInvalidValue;
         }
 #define FIT_T2(TX, TY, S)                                                                  \
@@ -47,7 +56,9 @@ cudaError_t launch_step_tma<float>(const StepArgs<float> &a, const TmaMaps &maps
 #undef FIT_T2
         return cudaErrorInvalidValue;
     }
+    if (a.gd) return cudaErrorInvalidValue;   // the difference output is a two-cell kernel epilogue
     if (a.gb) {   // the adjoint step with the gradient accumulation fused in
+        if (a.ge0 == nullptr) return cudaErrorInvalidValue;
         if (t.tx == 64 && t.ty == 4 && (t.stages == 0 || t.stages == 3))
             return lossy ? launch_one<float, 64, 4, 3, true, true>(a, maps, muarr, energy, s)
                          : launch_one<float, 64, 4, 3, false, true>(a, maps, muarr, energy, s);

@@ -61,7 +61,7 @@ class fit_run_opts(ctypes.Structure):
                 ("profile", ctypes.c_int), ("kernel", ctypes.c_int), ("stages", ctypes.c_int),
                 ("debug_wait_limit", ctypes.c_int), ("debug_extra_tx", ctypes.c_int),
                 ("homogeneous", ctypes.c_int), ("expo_substep", ctypes.c_int), ("expo_degree", ctypes.c_int),
-                ("expo_tol", ctypes.c_double), ("steps_per_launch", ctypes.c_int)]
+                ("expo_tol", ctypes.c_double), ("steps_per_launch", ctypes.c_int), ("adjoint_mem_mb", ctypes.c_int)]
 
 
 class fit_run_stats(ctypes.Structure):

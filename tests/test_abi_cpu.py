@@ -84,3 +84,32 @@ def test_injected_allocation_failure_gives_oom():
     assert out.value is None
     assert fitgb.strerror(rc) == "device out of memory"
 
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors of fit_run_opts, fit_source, fit_probe and
+    fit_run_stats have the C header's size and field offsets (gcc compiles the
+    header and prints them)."""
+    import ctypes
+    import shutil
+    from paper_1705_08019_gb300 import fitgb
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    structs = {"fit_run_opts": fitgb.fit_run_opts, "fit_source": fitgb.fit_source, "fit_probe": fitgb.fit_probe,
+               "fit_run_stats": fitgb.fit_run_stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fitgb.h"', 'int main(void) {']
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines.append('return 0; }')
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True, check=True)
+               .stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(out[name]) == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(out[f"{name}.{f}"]) == getattr(cls, f).offset, (name, f)

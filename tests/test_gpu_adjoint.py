@@ -188,3 +188,20 @@ def test_functional_without_gradient_matches_oracle(precision, tol):
         J2 = probe_energy(torch.from_numpy(w.eps_r).cuda(), w.spacing, dt, w.nsteps, w.sources, w.probes,
                           sigma=torch.from_numpy(w.sigma).cuda(), precision=precision)
     assert float(J2.item()) == float(J[0])
+
+
+def test_kept_forward_differences_give_the_same_gradient():
+    """With a memory budget the forward sweep keeps e^{n+1} - e^n of its last
+    checkpoint segments and the adjoint skips their recompute; the FP32
+    gradient and J are the same bits with none, some or all segments kept."""
+    w = small_case(dims=(64, 32, 32), nsteps=40)
+    dt = w.cfl_fraction * oracle.cfl_dt(w.dims, w.spacing, w.eps_r)
+    g = fitgb.Grid(w.dims, w.spacing, w.eps_r, None, w.sigma, 32)
+    ref = g.adjoint(dt, w.nsteps, w.sources, w.probes, ckpt_every=4)
+    per_step_mb = 3 * 64 * 32 * 32 * 4 / 2 ** 20
+    for budget in (int(5.5 * 4 * per_step_mb), 64, 1024):   # 5 of 10 segments, all, all
+        J, grad = g.adjoint(dt, w.nsteps, w.sources, w.probes, ckpt_every=4,
+                            opts=fitgb.make_opts(adjoint_mem_mb=budget))
+        assert J == ref[0]
+        assert np.array_equal(grad, ref[1]), budget
+    g.close()
