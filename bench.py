@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--compare-plain", action="store_true",
                     help="also time the K windows run one after another (members_per_pass=1)")
     ap.add_argument("--side", type=int, default=None, help="boxes workload: cells per side [256]")
-    ap.add_argument("--ncu-case", choices=["leapfrog", "paraexp", "solve", "expo", "batch"], default=None,
+    ap.add_argument("--ncu-case", choices=["leapfrog", "paraexp", "solve", "expo", "batch", "adjoint"], default=None,
                     help="run a short untimed case for an ncu capture and exit (no JSON line)")
     ap.add_argument("--ncu-steps", type=int, default=8)
     ap.add_argument("--ncu-members", type=int, default=4)
@@ -605,6 +605,25 @@ def ncu_case(args):
         torch.cuda.synchronize()
         for g in gs:
             fitgb.fit_grid_destroy(g)
+        return
+    if args.ncu_case == "adjoint":
+        # the 128^3 adjoint over --ncu-steps steps, checkpoints every 10, the last two segments' e^{n+1}-e^n
+        # kept: step launches 0..N/2-1 plain forward, N/2..N-1 forward keeping differences, then 20 fused
+        # adjoint steps reading kept differences, then per earlier segment 10 recompute + 10 fused adjoint
+        # steps reading two ring states
+        from paper_1705_08019_gb300 import workloads as W
+        w = W.adjoint128(nsteps=args.ncu_steps)
+        dev = torch.device("cuda", 0)
+        g = fitgb.fit_grid_create(w.dims, w.spacing, torch.from_numpy(w.eps_r).to(dev), None,
+                                  torch.from_numpy(w.sigma).to(dev), 32)
+        dt = w.cfl_fraction * fitgb.fit_cfl_dt(g)
+        nx, ny, nz = w.dims
+        per_step_mb = 3 * ((nx + 3) // 4 * 4) * ny * nz * 4 / 2 ** 20
+        grad = torch.zeros(tuple(reversed(w.dims)), dtype=torch.float64, device=dev)
+        fitgb.fit_adjoint_grad(g, dt, w.nsteps, w.sources, w.probes, 10, None, grad,
+                               fitgb.make_opts(adjoint_mem_mb=int(20.5 * per_step_mb)), torch.cuda.current_stream(dev))
+        torch.cuda.synchronize()
+        fitgb.fit_grid_destroy(g)
         return
     w = load_workload(args.workload, args)
     dev = torch.device("cuda", 0)
