@@ -442,6 +442,8 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.empty_cache()
         extras["adjoint"] = adjoint_section(fitgb, dev, stream, peak)
         torch.cuda.empty_cache()
+        extras["graded_leja"] = graded_leja_section(fitgb, dev, stream)
+        torch.cuda.empty_cache()
 
     e2e = None
     if not args.no_e2e:
@@ -500,7 +502,7 @@ def batched_section(args, fitgb, dev, stream, peak):
         fitgb.fit_grid_destroy(g)
     work = sum(work_of(w) for w in ws)
 
-    def solve(plain=False):
+    def solve(plain=False, profile=0):
         gs = [fitgb.fit_grid_create(w.dims, w.spacing, e, None, None, 32) for w, e in zip(ws, eps_d)]
         probs = [dict(grid=g, dt=dt, K=w.K, win=w.windows(), sources=w.sources, probes=w.probes, probe_out=o)
                  for g, dt, w, o in zip(gs, dts, ws, outs)]
@@ -509,21 +511,31 @@ def batched_section(args, fitgb, dev, stream, peak):
                 fitgb.paraexp_run(q["grid"], q["dt"], q["K"], q["win"], q["sources"], q["probes"], q["probe_out"],
                                   opts=fitgb.make_opts(members_per_pass=1), stream=stream)
         else:
-            fitgb.paraexp_run_batched(probs, fitgb.make_opts(use_graph=1, autotune=1), stream)
+            fitgb.paraexp_run_batched(probs, fitgb.make_opts(use_graph=1, autotune=1, profile=profile), stream)
+        sts = [fitgb.fit_last_stats(g) for g in gs]
         for g in gs:
             fitgb.fit_grid_destroy(g)
+        return sts
 
-    solve()   # autotuning and graph capture happen here
+    solve()   # autotuning happens here
     bms, _ = timed(stream, solve)
     ref = [o.clone() for o in outs]
     pms, _ = timed(stream, lambda: solve(plain=True))
     same = all(torch.equal(a, b) for a, b in zip(outs, ref))
-    alg = batch_alg_bytes(ws)
-    achieved = alg / (bms / 1e3) / 1e9
+    sts = solve(profile=1)   # the device time of the launch loop (graph launch), for the kernel roofline
+    loop_ms = sts[0]["step_ms"]
+    alg = sum(st["alg_bytes"] for st in sts)
+    assert abs(alg - batch_alg_bytes(ws)) <= 1e-9 * alg
+    achieved = alg / (loop_ms / 1e3) / 1e9
+    whole = alg / (bms / 1e3) / 1e9
     return {"workload": "batch64", "grids": len(ws), "cells": int(sum(w.ncells for w in ws)), "K": ws[0].K,
             "nsteps": ws[0].nsteps, "value": work / (bms / 1e3) / 1e9, "unit": UNIT, "seconds": bms / 1e3,
             "roofline": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "kernel": "batched_tma_kernel (whole solve time, launches and superposition included)"},
+                         "loop_s": loop_ms / 1e3, "whole_solve_frac": whole / peak,
+                         "kernel": "batched_tma2_kernel: the graph-launched iteration loop (the batched launches "
+                                   "and the superposition of finished members), CUDA events around the graph "
+                                   "launch; whole_solve_frac divides by the whole call (grid set-up, "
+                                   "coefficients, graph capture and instantiation included)"},
             "plain_per_window_s": pms / 1e3, "vs_plain": pms / bms, "probes_equal_to_plain": bool(same)}
 
 
@@ -876,23 +888,18 @@ def expo_report(args):
     print(json.dumps(out), flush=True)
 
 
-def graded_report(args):
+def graded_leja_section(fitgb, dev, stream):
     """The paper's claim behind R(k) on the GPU: on a strongly graded grid the
     exponential propagator advances a source-free state over an interval with
     fewer operator applications, and in less time, than the leapfrog at the
     step of eq. (cfl).  Grid: lossless 256^3 boxes with the central slab of
-    cells along each axis shrunk to d/k, FP32.  The state is that of a
-    300-step leapfrog run with the band source; both methods then cover the
-    same interval of n leapfrog steps (Leja with dense output at the same
-    steps), and the probe traces are compared."""
+    cells along each axis shrunk to d/k (k = 1: uniform), FP32.  The state is
+    that of a 300-step leapfrog run with the band source; both methods then
+    cover the same interval of 2000 leapfrog steps (Leja, eps_A = 1e-6, with
+    dense output at the same steps), each timed by CUDA events on the stream
+    (best of two), and the probe traces are compared."""
     import torch
-    from paper_1705_08019_gb300 import build as B
-    from paper_1705_08019_gb300 import fitgb
     from paper_1705_08019_gb300 import workloads as W
-    B.build()
-    fitgb.load()
-    dev = torch.device("cuda", 0)
-    s = torch.cuda.current_stream(dev)
     rows = []
     for k in (1, 20):
         w = W.boxes_graded(k)
@@ -901,25 +908,23 @@ def graded_report(args):
         dt = 0.95 * fitgb.fit_cfl_dt(g)
         e0 = torch.zeros((3,) + tuple(reversed(w.dims)), dtype=torch.float32, device=dev)
         h0 = torch.zeros_like(e0)
-        fitgb.fit_leapfrog_run(g, dt, 300, 0, w.sources, w.probes, None, None, e0, h0, stream=s)
+        fitgb.fit_leapfrog_run(g, dt, 300, 0, w.sources, w.probes, None, None, e0, h0, stream=stream)
         n = 2000
         res = {}
         for name in ("leapfrog", "leja"):
-            times = []
+            best = None
             for rep in range(2):
                 e, h = e0.clone(), h0.clone()
                 pr = torch.zeros((n, len(w.probes)), dtype=torch.float64, device=dev)
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
                 if name == "leapfrog":
-                    fitgb.fit_leapfrog_run(g, dt, n, 300, (), w.probes, pr, None, e, h, stream=s)
+                    fn = lambda: fitgb.fit_leapfrog_run(g, dt, n, 300, (), w.probes, pr, None, e, h, stream=stream)
                 else:
-                    fitgb.fit_expo_propagate(g, dt, n, w.probes, pr, e, h,
-                                             fitgb.make_opts(homogeneous="leja", expo_tol=1e-6, profile=1), s)
-                torch.cuda.synchronize()
-                times.append(time.perf_counter() - t0)
+                    fn = lambda: fitgb.fit_expo_propagate(g, dt, n, w.probes, pr, e, h,
+                                                          fitgb.make_opts(homogeneous="leja", expo_tol=1e-6), stream)
+                ms, _ = timed(stream, fn)
+                best = ms if best is None else min(best, ms)
             st = fitgb.fit_last_stats(g)
-            res[name] = (min(times), pr.cpu().numpy(), st)
+            res[name] = (best / 1e3, pr.cpu().numpy(), st)
         beta = fitgb.fit_spectral_bound(g)
         q, m = fitgb.fit_expo_plan("leja", dt * beta / 2, 1e-6, 32)
         fitgb.fit_grid_destroy(g)
@@ -932,7 +937,19 @@ def graded_report(args):
                      "leapfrog_s": res["leapfrog"][0], "leja_s": res["leja"][0],
                      "leja_over_leapfrog_time": res["leja"][0] / res["leapfrog"][0],
                      "probe_relerr_leja_vs_leapfrog": rel})
-    print(json.dumps({"study": "homogeneous propagation, graded 256^3 boxes", "rows": rows}), flush=True)
+    return {"study": "homogeneous propagation over 2000 steps, graded 256^3 lossless boxes (central slabs d/k)",
+            "rows": rows}
+
+
+def graded_report(args):
+    """graded_leja_section on its own (see there)."""
+    import torch
+    from paper_1705_08019_gb300 import build as B
+    from paper_1705_08019_gb300 import fitgb
+    B.build()
+    fitgb.load()
+    dev = torch.device("cuda", 0)
+    print(json.dumps(graded_leja_section(fitgb, dev, torch.cuda.current_stream(dev))), flush=True)
 
 
 def rk_report(args):

@@ -358,9 +358,13 @@ int batched_group(const std::vector<const fit_paraexp_problem *> &probs, bool lo
                 BatchHost &h = H[gi];
                 fit_grid *g = h.p->grid;
                 g->stats.step_launches += 1;
+                int active = 0;
                 for (int m = (int)h.specs.size() - 1; m >= 0; --m) {   // shortest first
                     const MemberSpec &sp = h.specs[h.order[m]];
-                    if (sp.start + it < sp.start + sp.nit) g->stats.cell_updates += g->ncell;
+                    if (sp.start + it < sp.start + sp.nit) {
+                        g->stats.cell_updates += g->ncell;
+                        ++active;
+                    }
                     if (sp.nit != it + 1 || !h.ae) continue;
                     const size_t n6 = 6 * (size_t)g->ncp;
                     const float *fin = (const float *)g->state.p + 2 * n6 * (size_t)m + ((it + 1) & 1) * n6;
@@ -368,20 +372,44 @@ int batched_group(const std::vector<const fit_paraexp_problem *> &probs, bool lo
                     if ((e = accumulate_state<float>(3 * g->ncp, fin + 3 * g->ncp, h.ah, cs)) != cudaSuccess)
                         return e;
                 }
+                // algorithmic bytes: each active member's fields in and out, the coefficients once
+                if (active > 0)
+                    g->stats.alg_bytes += (48.0 * active + (g->lossy ? 24.0 : 12.0) + (g->mu_array ? 12.0 : 0.0)) *
+                                          (double)g->ncell;
             }
         }
         return cudaSuccess;
     };
+    // opts->profile: the device time of the iteration loop (the batched launches and the
+    // superposition of finished members) by CUDA events on the stream, into every grid's stats
+    const bool profile = opts && opts->profile;
+    cudaEvent_t pe[2] = {nullptr, nullptr};
+    if (profile) {
+        FIT_CHECK(cudaEventCreate(&pe[0]));
+        FIT_CHECK(cudaEventCreate(&pe[1]));
+        if (!graph) FIT_CHECK(cudaEventRecord(pe[0], s));
+    }
     cudaError_t le = loop();
+    if (profile && !graph && le == cudaSuccess) le = cudaEventRecord(pe[1], s);
     if (graph) {
         cudaError_t ee = cudaStreamEndCapture(cs, &gr);
         if (le == cudaSuccess) le = ee;
         if (le == cudaSuccess) le = cudaGraphInstantiate(&ge, gr, 0);
+        if (le == cudaSuccess && profile) le = cudaEventRecord(pe[0], s);
         if (le == cudaSuccess) le = cudaGraphLaunch(ge, s);
+        if (le == cudaSuccess && profile) le = cudaEventRecord(pe[1], s);
         if (le == cudaSuccess) le = cudaStreamSynchronize(s);
         if (ge) cudaGraphExecDestroy(ge);
         if (gr) cudaGraphDestroy(gr);
         cudaStreamDestroy(cs);
+    }
+    if (profile) {
+        float ms = 0.f;
+        if (le == cudaSuccess) le = cudaEventSynchronize(pe[1]);
+        if (le == cudaSuccess) le = cudaEventElapsedTime(&ms, pe[0], pe[1]);
+        cudaEventDestroy(pe[0]);
+        cudaEventDestroy(pe[1]);
+        for (int gi = 0; gi < ng; ++gi) H[gi].p->grid->stats.step_ms = ms;
     }
     FIT_CHECK(le);
     // probe sums and final fields of each grid
