@@ -445,6 +445,7 @@ def run_ours(args, rank, world, local_rank):
         extras["graded_leja"] = graded_leja_section(fitgb, dev, stream)
         torch.cuda.empty_cache()
 
+
     e2e = None
     if not args.no_e2e:
         # the same solve through the C ABI with host buffers: materials H2D,
@@ -952,7 +953,7 @@ def graded_report(args):
     print(json.dumps(graded_leja_section(fitgb, dev, torch.cuda.current_stream(dev))), flush=True)
 
 
-def rk_report(args):
+def rk_section(fitgb):
     """R(k) = C_Leja(k) / C_LF(k) on the 2-D wave grid of Sec. IV-A with the
     central element shrunk to (d/k) x (d/k), over T = 2e-7 s.  Leapfrog takes
     the step of eq. (cfl); Leja interpolates on the library's bound
@@ -961,11 +962,7 @@ def rk_report(args):
     grid).  Counts are applications of A (a leapfrog step applies C and C~
     once: one application; the paper's C_LF = 2 n_t counts C and C~
     separately, reported as well)."""
-    from paper_1705_08019_gb300 import build as B
-    from paper_1705_08019_gb300 import fitgb
     from paper_1705_08019_gb300 import workloads as W
-    B.build()
-    fitgb.load()
     T = 2e-7
     rows = []
     for tol in (1e-2, 1e-8):
@@ -998,8 +995,16 @@ def rk_report(args):
             dt_out = T / n_lf
             q, m = fitgb.fit_expo_plan("leja", dt_out * beta / 2, 1e-2, 64)
             uni.append({"n_x": nxy, "n_t": nt, "leapfrog_steps": n_lf, "leja_applications": m * int(np.ceil(n_lf / q))})
-    print(json.dumps({"study": "R(k), 2-D wave grid, central element d/k", "T": T, "rows": rows,
-                      "uniform_mesh_cost": uni}), flush=True)
+    return {"study": "R(k), 2-D wave grid, central element d/k", "T": T, "rows": rows, "uniform_mesh_cost": uni}
+
+
+def rk_report(args):
+    """rk_section on its own (see there)."""
+    from paper_1705_08019_gb300 import build as B
+    from paper_1705_08019_gb300 import fitgb
+    B.build()
+    fitgb.load()
+    print(json.dumps(rk_section(fitgb)), flush=True)
 
 
 def adjoint_report(args):
