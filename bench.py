@@ -100,7 +100,9 @@ def load_workload(name, args=None):
     if name == "cavity16":
         return W.cavity16()
     if name == "boxes512":
-        return W.boxes512()
+        w = W.boxes512(**({"nsteps": args.nsteps} if args is not None and args.nsteps else {}))
+        w.precision = args.precision if args is not None and args.precision else 40
+        return w
     if name == "boxes256lossless":
         return W.boxes256_lossless()
     if name == "wave2d":
@@ -764,9 +766,10 @@ def run_batch(args, rank, world, local_rank):
 
 
 def accuracy_report(args):
-    """One FP32 ParaExp solve of the workload (FP64 superposition) and an FP64
-    sequential leapfrog over the first K/2 windows on the same float-rounded
-    coefficients; prints the probe error over those windows and the timings."""
+    """One FP32 ParaExp solve of the workload (FP64 superposition; --precision 32
+    or 40) and an FP64 sequential leapfrog over the first K/2 windows on the same
+    float-rounded coefficients; prints the probe error over those windows and
+    the timings."""
     import torch
     from paper_1705_08019_gb300 import build as B
     from paper_1705_08019_gb300 import fitgb
@@ -789,8 +792,9 @@ def accuracy_report(args):
     torch.cuda.synchronize()
     out["fp64_reference_s"] = time.perf_counter() - t0
     fitgb.fit_grid_destroy(g)
-    # FP32 ParaExp over all K windows
-    g = fitgb.fit_grid_create(w.dims, w.spacing, eps, None, sig, 32)
+    # FP32 ParaExp over all K windows (plain FP32 fields, or with the bfloat16 residual)
+    out["precision"] = PREC_NAME[w.precision]
+    g = fitgb.fit_grid_create(w.dims, w.spacing, eps, None, sig, w.precision)
     nt = int(win[-1] - win[0])
     pr = torch.zeros((nt, len(w.probes)), dtype=torch.float64, device=dev)
     ef = torch.zeros((3,) + tuple(reversed(w.dims)), dtype=torch.float64, device=dev)

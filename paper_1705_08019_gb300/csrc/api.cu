@@ -74,7 +74,26 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
     std::stable_sort(order.begin(), order.end(),
                      [&](int a, int b) { return specs_in[a].nit > specs_in[b].nit; });
     const int nm_total = (int)order.size();
-    const int mpp = (opts && opts->members_per_pass > 0) ? std::min(opts->members_per_pass, nm_total) : nm_total;
+    int mpp = (opts && opts->members_per_pass > 0) ? std::min(opts->members_per_pass, nm_total) : nm_total;
+    if (!(opts && opts->members_per_pass > 0) && nm_total > 1) {
+        // all members at once unless their states do not fit in the device memory left
+        // (a too-small state buffer is freed before the new one is taken, so it counts
+        // as free); then as many members per pass as fit, less a margin for the other
+        // workspaces of the call
+        const size_t per = 2 * n6 * sizeof(T);
+        size_t free_b = 0, total_b = 0;
+        if (g->state.n < per * (size_t)nm_total) {
+            if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+                const size_t avail = free_b + g->state.n;
+                const size_t margin = (size_t(1) << 30) + total_b / 64 +
+                                      (sum_mode == 1 && acc_e ? 2 * n6 * sizeof(float) : 0);
+                if (avail < margin + per * (size_t)nm_total)
+                    mpp = avail > margin + per ? (int)std::min<size_t>((avail - margin) / per, (size_t)nm_total) : 1;
+            } else {
+                cudaGetLastError();
+            }
+        }
+    }
 
     // workspaces
     if ((rc = ensure(g->state, 2 * n6 * sizeof(T) * (size_t)mpp))) return rc;
@@ -197,9 +216,14 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
     // Groups run from the end of the table (shortest members) to its start, and
     // inside a group members finish shortest first, so the superposition adds
     // members in decreasing table order whatever members_per_pass is.
-    for (int g_end = nm_total; g_end > 0; g_end -= mpp) {
-        const int first = std::max(0, g_end - mpp);
-        const int cnt = g_end - first;
+    // passes over groups of members, shortest group first (so members finish, and are
+    // superposed, in the one-pass order); the first group takes the remainder, so the
+    // long members that set the launch count share their launches with full groups
+    const int npass = (nm_total + mpp - 1) / mpp;
+    auto group = [&](int pass) { return pass == 0 ? nm_total - (npass - 1) * mpp : mpp; };
+    for (int pass = 0, g_end = nm_total; g_end > 0; g_end -= group(pass++)) {
+        const int cnt = group(pass);
+        const int first = g_end - cnt;
         std::vector<Member> mem(cnt);
         for (int q = 0; q < cnt; ++q) {
             const MemberSpec &sp = specs_in[order[first + q]];
