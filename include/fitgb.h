@@ -100,10 +100,11 @@ typedef struct {
     int sigma_scheme;           /* 0: sigma at (e^n+e^{n+1})/2, 1: at e^n [0] */
     int sum_mode;               /* superposition: 0 FP64, 1 Kahan FP32 [0]    */
     int members_per_pass;       /* ParaExp members advanced per launch;
-                                   0 = all K at once (batched), or as many as
-                                   the free device memory holds when the K
-                                   states do not fit; 1 = one member after
-                                   another (plain per-window runs) [0]        */
+                                   0 = all K at once (batched), or fewer when
+                                   their states pass 96 GiB (larger launches
+                                   run slower) or the free device memory;
+                                   1 = one member after another (plain
+                                   per-window runs) [0]                       */
     int force_dt;               /* 1: accept dt above the CFL estimate [0]    */
     int profile;                /* 1: time every step launch with CUDA events
                                    on the run's stream (fit_last_stats) [0]   */

@@ -76,19 +76,25 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
     const int nm_total = (int)order.size();
     int mpp = (opts && opts->members_per_pass > 0) ? std::min(opts->members_per_pass, nm_total) : nm_total;
     if (!(opts && opts->members_per_pass > 0) && nm_total > 1) {
-        // all members at once unless their states do not fit in the device memory left
-        // (a too-small state buffer is freed before the new one is taken, so it counts
-        // as free); then as many members per pass as fit, less a margin for the other
-        // workspaces of the call
+        // All members at once, within two limits.  (1) The member states advanced by one
+        // launch stay within kLaunchStateBytes: on GB300 a launch whose member states span
+        // more runs slower per cell-update (512^3 with residual fields: 27 members, 261 GB:
+        // 62.5 Gcell/s; 16: 71.5; 8: 73.7; 6: 74.1; plain FP32: 32 members, 206 GB: 113.8,
+        // 16: 117.3), while grids whose K states are smaller keep every member in one launch
+        // (256^3: 16 members, 19 GB, at the best rate).  (2) They fit in the device memory
+        // left (a too-small state buffer is freed before the new one is taken, so it counts
+        // as free), less a margin for the call's other workspaces.
+        constexpr size_t kLaunchStateBytes = size_t(96) << 30;
         const size_t per = 2 * n6 * sizeof(T);
+        mpp = (int)std::max<size_t>(1, std::min<size_t>((size_t)nm_total, kLaunchStateBytes / per));
         size_t free_b = 0, total_b = 0;
-        if (g->state.n < per * (size_t)nm_total) {
+        if (g->state.n < per * (size_t)mpp) {
             if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
                 const size_t avail = free_b + g->state.n;
                 const size_t margin = (size_t(1) << 30) + total_b / 64 +
                                       (sum_mode == 1 && acc_e ? 2 * n6 * sizeof(float) : 0);
-                if (avail < margin + per * (size_t)nm_total)
-                    mpp = avail > margin + per ? (int)std::min<size_t>((avail - margin) / per, (size_t)nm_total) : 1;
+                if (avail < margin + per * (size_t)mpp)
+                    mpp = avail > margin + per ? (int)std::min<size_t>((avail - margin) / per, (size_t)mpp) : 1;
             } else {
                 cudaGetLastError();
             }
