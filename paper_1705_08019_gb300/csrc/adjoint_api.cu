@@ -113,6 +113,24 @@ int adjoint_impl(fit_grid *g, double dt, long long N, const fit_source *src, int
     a.ch = (const T *)g->ch.p;
     a.nmem = 1;
     a.err = (int *)g->err.p;
+    {   // z chunks from the plain step kernel's CTAs per SM (unless the caller fixed them)
+        int per_sm = 0, nsm = 0, dev = 0;
+        cudaError_t qe = cudaGetDevice(&dev);
+        if (qe == cudaSuccess) qe = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (qe == cudaSuccess && !tile.kz_fixed) {
+            StepArgs<T> q = a;
+            q.occ_out = &per_sm;
+            qe = tile.kernel == 2 ? launch_step_tma<T>(q, ring_maps, tile, g->lossy, g->mu_array, false, s)
+                                  : launch_step<T>(q, tile, g->lossy, g->mu_array, false, s);
+        }
+        if (qe != cudaSuccess) {
+            cudaGetLastError();
+            per_sm = 0;
+        }
+        tile.kz = chunk_length(g, tile, 1, (long long)per_sm * nsm, nsm > 0 ? nsm : 152);
+        a.kz = tile.kz;
+        a.nchunk = (g->nz + tile.kz - 1) / tile.kz;
+    }
     // FP32 TMA runs fuse the gradient accumulation into the adjoint step
     const bool fused = fp32_blocks && tile.kernel == 2 && step_grad_supported(tile);
     // With a memory budget (opts->adjoint_mem_mb, two-cell FP32 kernel) the forward sweep keeps

@@ -219,12 +219,40 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
         a2.nchunk = (g->nz + a2.kz - 1) / a2.kz;
     }
 
-    // Groups run from the end of the table (shortest members) to its start, and
-    // inside a group members finish shortest first, so the superposition adds
-    // members in decreasing table order whatever members_per_pass is.
-    // passes over groups of members, shortest group first (so members finish, and are
-    // superposed, in the one-pass order); the first group takes the remainder, so the
-    // long members that set the launch count share their launches with full groups
+    // z chunks for the step launches of the largest group (unless the caller fixed
+    // them): from the step kernel's CTAs per SM, asked of the launch call itself
+    {
+        int per_sm = 0, nsm = 0, dev = 0;
+        cudaError_t qe = cudaGetDevice(&dev);
+        if (qe == cudaSuccess) qe = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (qe == cudaSuccess && !two && !tile.kz_fixed) {
+            StepArgs<T> q = a;
+            q.occ_out = &per_sm;
+            if (resf)
+                qe = launch_step_res((const StepArgs<float> &)q, maps, tile, g->lossy, g->mu_array, energy_dev != nullptr,
+                                     s);
+            else if (comp)
+                qe = launch_step_comp((const StepArgs<float> &)q, maps, tile, g->lossy, g->mu_array,
+                                      energy_dev != nullptr, s);
+            else if (tile.kernel == 2)
+                qe = launch_step_tma<T>(q, maps, tile, g->lossy, g->mu_array, energy_dev != nullptr, s);
+            else
+                qe = launch_step<T>(q, tile, g->lossy, g->mu_array, energy_dev != nullptr, s);
+        }
+        if (qe != cudaSuccess) {
+            cudaGetLastError();
+            per_sm = 0;
+        }
+        tile.kz = chunk_length(g, tile, mpp, (long long)per_sm * nsm, nsm > 0 ? nsm : 152);
+        a.kz = tile.kz;
+        a.nchunk = (g->nz + tile.kz - 1) / tile.kz;
+    }
+
+    // Passes over groups of members from the end of the table (shortest members) to
+    // its start, the first group taking the remainder, so that the long members that
+    // set the launch count share their launches with full groups.  Inside a group
+    // members finish shortest first, so the superposition adds members in decreasing
+    // table order whatever members_per_pass is.
     const int npass = (nm_total + mpp - 1) / mpp;
     auto group = [&](int pass) { return pass == 0 ? nm_total - (npass - 1) * mpp : mpp; };
     for (int pass = 0, g_end = nm_total; g_end > 0; g_end -= group(pass++)) {

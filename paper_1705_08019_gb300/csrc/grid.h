@@ -220,13 +220,44 @@ inline Tile pick_tile(const fit_grid *g, const fit_run_opts *o) {
         t.tx = 32;
         t.ty = 8;
     }
-    if (o && o->tile_z > 0) t.kz = o->tile_z;
     if (o && (o->stages == 3 || o->stages == 4)) t.stages = o->stages;
+    if (o && o->tile_z > 0) {   // the caller's chunk length, as given
+        t.kz = o->tile_z;
+        t.kz_fixed = true;
+    }
     if (t.kz <= 0) t.kz = 32;
-    // small grids: more z chunks so the GPU fills up
-    const long long cols = (long long)((g->nx + t.tx - 1) / t.tx) * ((g->ny + t.ty - 1) / t.ty);
-    while (t.kz > 8 && cols * ((g->nz + t.kz - 1) / t.kz) < 4 * 152) t.kz /= 2;
     return t;
+}
+
+// The z chunk length of a single-grid step launch over nmem members, at most
+// t.kz.  One CTA streams one chunk of one tile column, loading its planes plus
+// up to two beyond it (the plane below, whose h it recomputes, and the plane
+// above).  With `slots` CTAs resident on the GPU at once, a launch of B CTAs
+// runs in about ceil(B / slots) rounds, each as long as one CTA's planes; the
+// length that minimizes rounds x (kz + 2) is taken, the longest on ties.  On
+// GB300 this orders the measured launch times of single-member 128^3 and 256^3
+// grids correctly, where a chunk that leaves a last, partly filled round costs
+// up to a quarter of the step.  slots <= 0 (occupancy unknown): the chunk is
+// halved down to 8 planes while the launch has fewer CTAs than 4 per SM.
+inline int chunk_length(const fit_grid *g, const Tile &t, int nmem, long long slots, int nsm) {
+    const long long cols = (long long)((g->nx + t.tx - 1) / t.tx) * ((g->ny + t.ty - 1) / t.ty);
+    int kz = std::max(1, std::min(t.kz, g->nz));
+    if (t.kz_fixed) return t.kz;
+    if (slots <= 0) {
+        while (kz > 8 && cols * nmem * ((g->nz + kz - 1) / kz) < 4LL * nsm) kz /= 2;
+        return kz;
+    }
+    long long best = -1;
+    int best_kz = kz;
+    for (int k = kz; k >= 1; --k) {
+        const long long blocks = cols * nmem * ((g->nz + k - 1) / k);
+        const long long cost = ((blocks + slots - 1) / slots) * (k + 2);
+        if (best < 0 || cost < best) {
+            best = cost;
+            best_kz = k;
+        }
+    }
+    return best_kz;
 }
 
 

@@ -91,7 +91,17 @@ struct StepArgs {
     // forward sweep keeping e^{n+1} - e^n for the adjoint (FP32 two-cell TMA kernel; null = off):
     // 3 pitched components; an adjoint step then takes them in ge1 with ge0 null
     float *gd;
+    // set: a launch call launches nothing and stores how many CTAs of the kernel it
+    // would launch fit on one SM
+    int *occ_out;
 };
+
+// The occupancy answer of a launch call made with StepArgs::occ_out set.
+template <typename K>
+inline cudaError_t report_occupancy(K kernel, int threads, size_t dyn_smem, int *out) {
+    *out = 0;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, kernel, threads, dyn_smem);
+}
 
 // One grid of a batched launch (device table).
 template <typename T>
@@ -131,6 +141,7 @@ struct Tile {
     int kernel;      // 1: shared-memory staging by plain loads, 2: TMA pipeline
     int stages = 0;  // TMA ring depth (0: the tile's default)
     bool single = false;   // FP32 TMA kernels: one cell per thread instead of two
+    bool kz_fixed = false; // kz given by the caller (else chosen per run, see chunk_length)
 };
 
 // step.cu: plain-load staging kernel

@@ -330,6 +330,7 @@ __global__ void __launch_bounds__(TX *TY) step_kernel(const StepArgs<T> a) {
 
 template <typename T, int TX, int TY>
 cudaError_t launch_tile(const StepArgs<T> &a, bool lossy, bool muarr, bool energy, cudaStream_t s) {
+    if (a.occ_out) return report_occupancy(step_kernel<T, TX, TY, true, false, false>, TX * TY, 0, a.occ_out);
     const long long blocks = (long long)a.nmem * a.tiles_x * a.tiles_y * a.nchunk;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;

@@ -383,6 +383,7 @@ cudaError_t launch(const StepArgs<float> &a, const TmaMaps &maps, bool muarr, bo
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
+    if (a.occ_out) return report_occupancy(step_comp_kernel<TX, TY, S, LOSSY>, TX * TY, G::DYN_SMEM, a.occ_out);
     const long long blocks = (long long)a.nmem * a.tiles_x * a.tiles_y * a.nchunk;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;

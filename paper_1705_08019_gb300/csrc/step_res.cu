@@ -821,6 +821,7 @@ cudaError_t launch2(const StepArgs<float> &a, const TmaMaps &maps, bool muarr, b
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
+    if (a.occ_out) return report_occupancy(step_res2_kernel<TX, TY, S, LOSSY>, TX / 2 * TY, G::DYN_SMEM, a.occ_out);
     const long long blocks = (long long)a.nmem * a.tiles_x * a.tiles_y * a.nchunk;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
@@ -839,6 +840,7 @@ cudaError_t launch(const StepArgs<float> &a, const TmaMaps &maps, bool muarr, bo
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
+    if (a.occ_out) return report_occupancy(step_res_kernel<TX, TY, S, LOSSY>, TX * TY, G::DYN_SMEM, a.occ_out);
     const long long blocks = (long long)a.nmem * a.tiles_x * a.tiles_y * a.nchunk;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;

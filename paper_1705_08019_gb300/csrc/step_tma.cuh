@@ -545,6 +545,7 @@ cudaError_t launch_one(const StepArgs<T> &a, const TmaMaps &maps, bool muarr, bo
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
+    if (a.occ_out) return report_occupancy(step_tma_kernel<T, TX, TY, S, LOSSY, GRAD>, TX * TY, G::DYN_SMEM, a.occ_out);
     const long long blocks = (long long)a.nmem * a.tiles_x * a.tiles_y * a.nchunk;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;

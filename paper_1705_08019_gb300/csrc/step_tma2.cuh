@@ -452,6 +452,8 @@ cudaError_t launch_two(const StepArgs<float> &a, const TmaMaps &maps, bool muarr
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
+    if (a.occ_out)
+        return report_occupancy(step_tma2_kernel<TX, TY, S, LOSSY, EXTRA>, TX / 2 * TY, G::DYN_SMEM, a.occ_out);
     const long long blocks = (long long)a.nmem * a.tiles_x * a.tiles_y * a.nchunk;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
