@@ -419,6 +419,16 @@ int fit_leapfrog_run_static(int nx, int ny, int nz, double dx, double dy, double
  * FIT_ERR_OOM and leaves its grid usable.  The paper has no counterpart. */
 int fit_debug_fail_alloc(long long after);
 
+/* Test hook for the z chunk length of the single-grid step launches (host
+ * only, no device call): the chunk length, at most kz_max planes, that the
+ * library takes for an nx x ny x nz grid cut into tile_x x tile_y tile
+ * columns when a launch advances nmem members and `slots` CTAs of the step
+ * kernel are resident on the GPU at once.  It minimizes ceil(CTAs / slots) x
+ * (chunk + 2), the longest chunk on ties; slots <= 0 gives the fallback rule
+ * (halving from kz_max to 8 planes while the launch has fewer than 4 CTAs per
+ * SM of 152 SMs).  Returns the length, or FIT_ERR_ARG for a size below 1. */
+int fit_debug_chunk_length(int nx, int ny, int nz, int tile_x, int tile_y, int kz_max, int nmem, long long slots);
+
 /* Wait for the grid's outstanding work on `stream` and return the first
  * deferred device error, if any. */
 int fit_sync(fit_grid *g, void *stream);

@@ -127,7 +127,7 @@ int adjoint_impl(fit_grid *g, double dt, long long N, const fit_source *src, int
             cudaGetLastError();
             per_sm = 0;
         }
-        tile.kz = chunk_length(g, tile, 1, (long long)per_sm * nsm, nsm > 0 ? nsm : 152);
+        tile.kz = chunk_length(g->nx, g->ny, g->nz, tile, 1, (long long)per_sm * nsm, nsm > 0 ? nsm : 152);
         a.kz = tile.kz;
         a.nchunk = (g->nz + tile.kz - 1) / tile.kz;
     }

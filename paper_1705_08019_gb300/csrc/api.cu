@@ -243,7 +243,7 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
             cudaGetLastError();
             per_sm = 0;
         }
-        tile.kz = chunk_length(g, tile, mpp, (long long)per_sm * nsm, nsm > 0 ? nsm : 152);
+        tile.kz = chunk_length(g->nx, g->ny, g->nz, tile, mpp, (long long)per_sm * nsm, nsm > 0 ? nsm : 152);
         a.kz = tile.kz;
         a.nchunk = (g->nz + tile.kz - 1) / tile.kz;
     }
@@ -782,6 +782,12 @@ int fit_last_stats(const fit_grid *g, fit_run_stats *out) {
 int fit_debug_fail_alloc(long long after) {
     g_fail_alloc.store(after < 0 ? -1 : after);
     return FIT_OK;
+}
+
+int fit_debug_chunk_length(int nx, int ny, int nz, int tile_x, int tile_y, int kz_max, int nmem, long long slots) {
+    if (nx < 1 || ny < 1 || nz < 1 || tile_x < 1 || tile_y < 1 || kz_max < 1 || nmem < 1) return FIT_ERR_ARG;
+    Tile t{tile_x, tile_y, kz_max, 2};
+    return chunk_length(nx, ny, nz, t, nmem, slots, 152);
 }
 
 int fit_sync(fit_grid *g, void *stream) {

@@ -239,18 +239,18 @@ inline Tile pick_tile(const fit_grid *g, const fit_run_opts *o) {
 // grids correctly, where a chunk that leaves a last, partly filled round costs
 // up to a quarter of the step.  slots <= 0 (occupancy unknown): the chunk is
 // halved down to 8 planes while the launch has fewer CTAs than 4 per SM.
-inline int chunk_length(const fit_grid *g, const Tile &t, int nmem, long long slots, int nsm) {
-    const long long cols = (long long)((g->nx + t.tx - 1) / t.tx) * ((g->ny + t.ty - 1) / t.ty);
-    int kz = std::max(1, std::min(t.kz, g->nz));
+inline int chunk_length(int nx, int ny, int nz, const Tile &t, int nmem, long long slots, int nsm) {
+    const long long cols = (long long)((nx + t.tx - 1) / t.tx) * ((ny + t.ty - 1) / t.ty);
+    int kz = std::max(1, std::min(t.kz, nz));
     if (t.kz_fixed) return t.kz;
     if (slots <= 0) {
-        while (kz > 8 && cols * nmem * ((g->nz + kz - 1) / kz) < 4LL * nsm) kz /= 2;
+        while (kz > 8 && cols * nmem * ((nz + kz - 1) / kz) < 4LL * nsm) kz /= 2;
         return kz;
     }
     long long best = -1;
     int best_kz = kz;
     for (int k = kz; k >= 1; --k) {
-        const long long blocks = cols * nmem * ((g->nz + k - 1) / k);
+        const long long blocks = cols * nmem * ((nz + k - 1) / k);
         const long long cost = ((blocks + slots - 1) / slots) * (k + 2);
         if (best < 0 || cost < best) {
             best = cost;

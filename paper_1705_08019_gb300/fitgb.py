@@ -35,7 +35,8 @@ HOMOG = {"leapfrog": HOMOG_LEAPFROG, "leja": HOMOG_LEJA, "taylor": HOMOG_TAYLOR}
 EXPORTED = ("fit_grid_create", "fit_grid_destroy", "fit_cfl_dt", "fit_grid_info", "fit_leapfrog_run",
             "paraexp_run", "paraexp_run_batched", "fit_adjoint_grad", "fit_sync", "fit_strerror",
             "fit_version", "fit_last_stats", "fit_leapfrog_run_static", "fit_expo_plan", "fit_expo_coeffs",
-            "fit_expo_propagate", "fit_grid_create_graded", "fit_spectral_bound", "fit_debug_fail_alloc")
+            "fit_expo_propagate", "fit_grid_create_graded", "fit_spectral_bound", "fit_debug_fail_alloc",
+            "fit_debug_chunk_length")
 
 
 class FitError(RuntimeError):
@@ -127,6 +128,8 @@ def load():
         lib.fit_sync.restype = I
         lib.fit_debug_fail_alloc.argtypes = [ctypes.c_longlong]
         lib.fit_debug_fail_alloc.restype = I
+        lib.fit_debug_chunk_length.argtypes = [I, I, I, I, I, I, I, ctypes.c_longlong]
+        lib.fit_debug_chunk_length.restype = I
         lib.fit_strerror.argtypes = [I]
         lib.fit_strerror.restype = ctypes.c_char_p
         lib.fit_version.argtypes = []
@@ -139,6 +142,17 @@ def fit_debug_fail_alloc(after: int):
     """Test hook: the device allocation `after` allocations from now fails as
     out of memory (negative: off)."""
     _check(load().fit_debug_fail_alloc(int(after)), "fit_debug_fail_alloc")
+
+
+def fit_debug_chunk_length(dims, tile, kz_max, nmem, slots):
+    """Test hook: the z chunk length the library takes for a single-grid step
+    launch (host computation, no device call)."""
+    nx, ny, nz = dims
+    r = load().fit_debug_chunk_length(int(nx), int(ny), int(nz), int(tile[0]), int(tile[1]), int(kz_max), int(nmem),
+                                      int(slots))
+    if r < 0:
+        _check(r, "fit_debug_chunk_length")
+    return r
 
 
 def strerror(status: int) -> str:
