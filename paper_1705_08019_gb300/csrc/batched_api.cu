@@ -95,6 +95,10 @@ int batch_layout(std::vector<BatchHost> &H, Tile tile, bool lossy, std::vector<G
     gds.assign(ng, GridDesc<float>());
     maps.assign(ng, TmaMaps());
     items.clear();
+    // items of a tile column's last, shorter chunk go to the end of the list, longest
+    // first, so that the CTAs' last items of a launch are short and the launch ends
+    // with little idle time; members of one (grid, tile, chunk) stay adjacent
+    std::vector<std::pair<int, WorkItem>> tail;
     for (int gi = 0; gi < ng; ++gi) {
         fit_grid *g = H[gi].p->grid;
         GridDesc<float> &d = gds[gi];
@@ -123,10 +127,17 @@ int batch_layout(std::vector<BatchHost> &H, Tile tile, bool lossy, std::vector<G
         if (!encode_tma_maps(&maps[gi], 4, g->nx, g->ny, g->nz, g->pitch, g->state.p, 2 * K, g->coef.p,
                              lossy ? 6 : 3, tile.tx, tile.ty))
             return FIT_ERR_UNSUPPORTED;
+        const int last_len = g->nz - (d.nchunk - 1) * d.kz;   // planes of the last chunk
         for (int t = 0; t < d.tiles_x * d.tiles_y; ++t)
             for (int c = 0; c < d.nchunk; ++c)
-                for (int q = 0; q < K; ++q) items.push_back({gi, q, t, c});
+                for (int q = 0; q < K; ++q) {
+                    if (c == d.nchunk - 1 && last_len < d.kz) tail.push_back({last_len, WorkItem{gi, q, t, c}});
+                    else items.push_back({gi, q, t, c});
+                }
     }
+    std::stable_sort(tail.begin(), tail.end(),
+                     [](const std::pair<int, WorkItem> &a, const std::pair<int, WorkItem> &b) { return a.first > b.first; });
+    for (const auto &e : tail) items.push_back(e.second);
     return FIT_OK;
 }
 
