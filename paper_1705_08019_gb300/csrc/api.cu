@@ -219,8 +219,12 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
         a2.nchunk = (g->nz + a2.kz - 1) / a2.kz;
     }
 
-    // z chunks for the step launches of the largest group (unless the caller fixed
-    // them): from the step kernel's CTAs per SM, asked of the launch call itself
+    // z chunks (unless the caller fixed them): from the step kernel's CTAs per SM, asked
+    // of the launch call itself, for the largest group here and again for every launch
+    // whose number of active members differs from the previous one's
+    const Tile chunk_tile = tile;   // the tile's default chunk as the longest
+    long long chunk_slots = 0;
+    int chunk_nsm = 152;
     {
         int per_sm = 0, nsm = 0, dev = 0;
         cudaError_t qe = cudaGetDevice(&dev);
@@ -243,10 +247,13 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
             cudaGetLastError();
             per_sm = 0;
         }
-        tile.kz = chunk_length(g->nx, g->ny, g->nz, tile, mpp, (long long)per_sm * nsm, nsm > 0 ? nsm : 152);
+        chunk_slots = (long long)per_sm * nsm;
+        chunk_nsm = nsm > 0 ? nsm : 152;
+        tile.kz = chunk_length(g->nx, g->ny, g->nz, chunk_tile, mpp, chunk_slots, chunk_nsm);
         a.kz = tile.kz;
         a.nchunk = (g->nz + tile.kz - 1) / tile.kz;
     }
+    int chunk_members = mpp;   // the member count a.kz was chosen for
 
     // Passes over groups of members from the end of the table (shortest members) to
     // its start, the first group taking the remainder, so that the long members that
@@ -383,6 +390,11 @@ int run_members(fit_grid *g, double dt, int scheme, const std::vector<MemberSpec
         for (long long it = 0; !two && it < nit_max; ++it) {
             while (active > 0 && specs_in[order[first + active - 1]].nit <= it) --active;
             a.nmem = active;
+            if (active != chunk_members && chunk_slots > 0 && !two) {
+                a.kz = chunk_length(g->nx, g->ny, g->nz, chunk_tile, active, chunk_slots, chunk_nsm);
+                a.nchunk = (g->nz + a.kz - 1) / a.kz;
+                chunk_members = active;
+            }
             a.it = (int)it;
             a.parity = (int)(it & 1);
             if (profile) {
